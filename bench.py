@@ -1,0 +1,341 @@
+"""Benchmark of the Shan-Chen droplet/bubble hot path (one JSON line on rank 0).
+
+Workload (the 128^3 plain-method configuration): a droplet and a bubble of
+radius 32 in periodic 128^3 boxes, psi = 1 - exp(-n), G = -5, tau = 1, E4
+stencil, populations stored shifted in FP32 (FP64 observables).  One bench
+step = one convergence interval of the paper (2^11 lattice-Boltzmann steps)
+on both lattices, followed by the convergence/observable pass (pressure tensor
+samples, FP64 reductions, R_e, Delta P, C, R_s) on both.  value = lattice
+updates per second over all ranks (MLUPS).
+
+--impl reference times the FP64 CPU oracle on the same workload and metric
+(a bounded sample: one lattice-Boltzmann step per lattice per bench step).
+Multi-GPU (torchrun): every rank advances its own pair of lattices (the sweep
+shards into independent lattices; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+SIZE = 128
+RADIUS = 32.0
+G = -5.0
+TAU = 1.0
+RHO_L, RHO_G = 2.0, 0.15          # initial tanh densities of the workload
+LBM_STEPS_PER_STEP = 2048         # the paper's convergence interval
+BYTES_PER_LU = {"f64": 304, "f32": 152, "f16": 76}   # 19 loads + 19 stores per node
+WORKLOAD = ("two 128^3 periodic lattices (droplet R=32, bubble R=32), psi=1-exp(-n), G=-5, "
+            "tau=1, D3Q19 E4 Guo-BGK; 2048 LB steps + convergence/observable pass per step")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peak_gbs():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        try:
+            return float(json.loads(p.read_text())["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def bench_reference(args):
+    """FP64 CPU oracle on the same workload: one LB step per lattice per bench step."""
+    import numpy as np  # noqa: F401
+    from oracle import eos as E
+    from oracle import lbm3d
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    m = lbm3d.Model(tau=TAU, G=G, eos=E.EOS("one_minus_exp"))
+    c = (SIZE // 2,) * 3
+    lattices = [lbm3d.init_from_density(lbm3d.drop_density((SIZE,) * 3, c, RADIUS, a, b))
+                for a, b in ((RHO_L, RHO_G), (RHO_G, RHO_L))]
+
+    def one():
+        for k in range(len(lattices)):
+            lattices[k] = lbm3d.step(lattices[k], m)
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = time.perf_counter() - t0
+    lu = len(lattices) * SIZE ** 3 * args.steps
+    val = lu / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "reference_step": "1 LB step per lattice (bounded sample)"},
+        "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} x (1 LB step of each 128^3 lattice), numpy FP64"},
+        "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample(seconds_target=12.0):
+    """The oracle as it stands on this host: 128^3 lattice, whole LB steps until ~12 s."""
+    from oracle import eos as E
+    from oracle import lbm3d
+    m = lbm3d.Model(tau=TAU, G=G, eos=E.EOS("one_minus_exp"))
+    f = lbm3d.init_from_density(lbm3d.drop_density((SIZE,) * 3, (SIZE // 2,) * 3, RADIUS, RHO_L, RHO_G))
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds_target or n == 0:
+        f = lbm3d.step(f, m)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": SIZE ** 3 * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{n} LB steps of the 128^3 droplet lattice, numpy FP64, single thread"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-leg", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return bench_reference(args)
+
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2105_08772_gb300 as P
+
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    c = (SIZE // 2,) * 3
+
+    def make(prec):
+        with torch.cuda.stream(stream):
+            lats = [P.Lattice(SIZE, SIZE, SIZE, tau=TAU, G=G, psi="one_minus_exp", stencil="E4",
+                              prec=prec, stream=stream) for _ in range(2)]
+        lats[0].init_drop(c, RADIUS, RHO_L, RHO_G)
+        lats[1].init_drop(c, RADIUS, RHO_G, RHO_L)
+        return lats
+
+    lats = make(args.prec)
+    if args.autotune:
+        for lat in lats:
+            lat.autotune(reps=8)
+            lat.init_drop(c, RADIUS, RHO_L if lat is lats[0] else RHO_G, RHO_G if lat is lats[0] else RHO_L)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+
+    def bench_step(record):
+        kern_ms = 0.0
+        for k, lat in enumerate(lats):
+            if record:
+                ev[k][0].record(stream)
+            lat.step(LBM_STEPS_PER_STEP)
+            if record:
+                ev[k][1].record(stream)
+            lat.observables()          # synchronises the stream
+            if record:
+                kern_ms += ev[k][0].elapsed_time(ev[k][1])
+        return kern_ms
+
+    for _ in range(args.warmup):
+        bench_step(False)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    kern_ms = 0.0
+    with ClockSampler(dev) as clk:
+        t_start.record(stream)
+        for _ in range(args.steps):
+            kern_ms += bench_step(True)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if ws > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    N = SIZE ** 3
+    lu_rank = len(lats) * N * LBM_STEPS_PER_STEP * args.steps
+    value = lu_rank * ws / (elapsed_ms * 1e-3) / 1e6
+    launches_per_step = len(lats) * (LBM_STEPS_PER_STEP + 3)
+
+    # roofline of the dominant kernel (the fused step): algorithmic bytes per launch over the
+    # average launch time seen by CUDA events around the step-only part of the timed region
+    peak, peak_kind = measured_peak_gbs()
+    n_launch = len(lats) * LBM_STEPS_PER_STEP * args.steps
+    avg_launch_s = kern_ms * 1e-3 / n_launch
+    bytes_per_launch = BYTES_PER_LU[args.prec] * N
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    traffic = None
+    tr_path = ROOT / "profiles" / f"traffic_step_{args.prec}_128.json"
+    if tr_path.exists():
+        try:
+            traffic = json.loads(tr_path.read_text()).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # end to end through the public API with host buffers
+    host = []
+    for lat in lats:
+        pinned = torch.empty((SIZE, SIZE, SIZE), dtype=torch.float64, pin_memory=True)
+        pinned.numpy()[...] = lat.rho()
+        host.append(pinned)
+    for k, lat in enumerate(lats):        # warm the host path once
+        lat.init_rho(host[k].numpy())
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for k, lat in enumerate(lats):
+            lat.init_rho(host[k].numpy())
+            lat.step(LBM_STEPS_PER_STEP)
+            lat.observables()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = len(lats) * N * LBM_STEPS_PER_STEP * e2e_steps * ws / e2e_s / 1e6
+
+    fp64 = None
+    if not args.no_fp64_leg and args.prec != "f64":
+        lat64 = make("f64")[0]
+        lat64.step(LBM_STEPS_PER_STEP)
+        lat64.observables()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat64.step(LBM_STEPS_PER_STEP)
+        e1.record(stream)
+        lat64.observables()
+        ms = e0.elapsed_time(e1)
+        fp64 = {"value": N * LBM_STEPS_PER_STEP / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+                "sample": "one 2048-step interval of the 128^3 droplet, FP64 storage and arithmetic",
+                "hbm_gbs": BYTES_PER_LU["f64"] * N * LBM_STEPS_PER_STEP / (ms * 1e-3) / 1e9}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline or ws > 1 else cpu_baseline_sample()
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec != "f64" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "box": SIZE, "lattices_per_gpu": len(lats),
+                   "storage": {"f32": "f32 shifted", "f16": "f16 shifted, 2^k scale", "f64": "f64"}[args.prec],
+                   "lb_steps_per_step": LBM_STEPS_PER_STEP,
+                   "l2": "inputs larger than L2: 2 lattices x 2 population buffers x 159 MB",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                     "kernel": "lattice_kernel (fused pull + psi halo + Guo-BGK + store)",
+                     "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": len(lats) * N * 8,
+                "d2h_bytes_per_step": len(lats) * 152, "steps": e2e_steps},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "fp64": fp64,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * lbm.h -- C ABI of the GB300 Shan-Chen droplet/bubble library (liblbm.so).
+ *
+ * Method: "A Mesoscale Perspective on the Tolman Length" (arXiv:2105.08772).
+ *   Sec. II   D3Q19 BGK + Guo-forcing lattice Boltzmann step with the
+ *             Shan-Chen pseudopotential force, Eqs. (3)-(8), and the lattice
+ *             pressure tensor, Eq. (9).
+ *   Sec. III  generalised surface tension sigma[R], Eqs. (21)-(22), surface of
+ *             tension R_s, Laplace law Eq. (12), Tolman expansion Eq. (2).
+ *   Sec. IV   droplet/bubble set-up (Eq. (23)), P_in/P_out sampling, centre-of-
+ *             mass acceptance, the two convergence criteria, equimolar radius.
+ *
+ * Conventions shared by every entry point
+ *   - Device memory: the caller allocates and owns all device memory (the
+ *     "workspace") and the CUDA stream; the library only borrows them and
+ *     never calls cudaMalloc/cudaFree.  Size the workspace with
+ *     lbm_workspace_bytes / lbm_batch_workspace_bytes; it must be 256-byte
+ *     aligned and stay valid until the context is destroyed.
+ *   - Streams: every device operation is enqueued on the context's stream
+ *     (a cudaStream_t passed as void*; NULL = legacy default stream).  Calls
+ *     documented "async" return before the GPU work finishes; calls that
+ *     return host data synchronise that stream first.
+ *   - Host buffers: plain C arrays owned by the caller; the library never
+ *     keeps a pointer to them after the call returns.
+ *   - Errors: every call returns an lbm_status and never aborts, traps or
+ *     exits.  On failure lbm_last_error(ctx) holds a one-line message.  A CUDA
+ *     error is reported as LBM_ECUDA.  Arguments are checked before any work is
+ *     enqueued (LBM_EINVAL).
+ *   - Field layout: a scalar field of a box (nx, ny, nz) is a contiguous
+ *     double array indexed (z*ny + y)*nx + x.  Populations are 19 such planes,
+ *     population i at offset i*nx*ny*nz, in this velocity order:
+ *        0:( 0, 0, 0)
+ *        1:(+1, 0, 0)  2:(-1, 0, 0)  3:( 0,+1, 0)  4:( 0,-1, 0)
+ *        5:( 0, 0,+1)  6:( 0, 0,-1)
+ *        7:(+1,+1, 0)  8:(-1,-1, 0)  9:(+1,-1, 0) 10:(-1,+1, 0)
+ *       11:(+1, 0,+1) 12:(-1, 0,-1) 13:(+1, 0,-1) 14:(-1, 0,+1)
+ *       15:( 0,+1,+1) 16:( 0,-1,-1) 17:( 0,+1,-1) 18:( 0,-1,+1)
+ *     The box is periodic in all three axes.
+ *   - The centre node is c = (nx/2, ny/2, nz/2) (integer division), the
+ *     "farthest corner" is ((c_a + n_a/2) mod n_a) per axis (for odd sizes
+ *     this is (n-1, n-1, n-1), the node Sec. IV names).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+typedef struct lbm_batch lbm_batch;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,      /* bad argument (sizes, tau <= 1/2, G >= G_c, null pointer, ...) */
+    LBM_ENOMEM = 2,      /* the caller's workspace is too small */
+    LBM_ECUDA = 3,       /* a CUDA runtime call failed */
+    LBM_ENUMERIC = 4,    /* NaN/Inf or a non-positive density found in the field */
+    LBM_ENOTCONV = 5,    /* max_steps reached before either convergence test passed */
+    LBM_ENOMIN = 6,      /* result status: sigma[R] has no minimum (C / Delta P <= 0) */
+    LBM_ECOLLAPSE = 7,   /* result status: |n_in - n_out| below 1e-2 of the initial contrast */
+    LBM_EOFFCENTER = 8,  /* result status: a centre-of-mass coordinate is > 1e-3 off centre */
+    LBM_ETIMEOUT = 9     /* reserved for bounded device-side waits */
+} lbm_status;
+
+/* psi(n) kinds (Sec. II below Eq. (8); Sec. IV names the first two). */
+typedef enum {
+    LBM_PSI_EXP_INV = 0,        /* psi = exp(-1/n)                                   */
+    LBM_PSI_ONE_MINUS_EXP = 1,  /* psi = 1 - exp(-n)                                 */
+    LBM_PSI_CS = 2              /* psi = sqrt(2 (p_CS(n) - n c_s^2) / (G c_s^2)),
+                                   Carnahan-Starling p_CS with a, b, Rgas, T below    */
+} lbm_psi_kind;
+
+typedef struct {
+    int kind;                   /* lbm_psi_kind */
+    double a, b, Rgas, T;       /* Carnahan-Starling constants; ignored unless kind == LBM_PSI_CS */
+} lbm_eos;
+
+/* Isotropic forcing stencils for Eq. (8): E4 is the paper's 18-vector
+ * D3Q19 stencil with W(1) = 1/6, W(2) = 1/12; E6 (32 vectors, shells
+ * |xi|^2 = 1..4) and E8 (92 vectors, shells 1,2,3,4,5,6,8) are the
+ * higher-order isotropic stencils the paper cites for the force. */
+typedef enum { LBM_E4 = 4, LBM_E6 = 6, LBM_E8 = 8 } lbm_stencil;
+
+/* Population storage.  F64: plain doubles, FP64 arithmetic.  F32_SHIFTED:
+ * f_i - w_i n0 stored as float, FP32 collision.  F16_SHIFTED: (f_i - w_i n0)
+ * times a per-lattice power of two stored as IEEE half, FP32 collision.  All
+ * observables and reductions are FP64 in every mode. */
+typedef enum { LBM_F64 = 0, LBM_F32_SHIFTED = 1, LBM_F16_SHIFTED = 2 } lbm_prec;
+
+typedef struct { int nx, ny, nz; } lbm_box;
+
+/* Observables of one lattice (Sec. III, Sec. IV).  status_bits: bit 0 no
+ * minimum of sigma[R], bit 1 collapsed, bit 2 off-centre, bit 3 non-finite
+ * field.  criterion: 0 none, 1 the Delta P test fired, 2 the delta-u test. */
+typedef struct {
+    double n_in, n_out;         /* density at the centre node and the farthest corner       */
+    double P_in, P_out, dP;     /* P^xx of Eq. (9) at those nodes; dP = P_in - P_out         */
+    double mass;                /* M = sum_x n                                              */
+    double com[3];              /* centre of mass of n - n_out (minimum image about c)       */
+    double R_e;                 /* equimolar radius (Sec. IV, last paragraph)                 */
+    double C, D;                /* int r^2 (P_out - P_T) dr and int r (P_out - P_T) dr        */
+    double R_s;                 /* surface of tension (6 C / dP)^(1/3); NaN if no minimum      */
+    double sigma_s;             /* sigma[R_s] = dP R_s / 2 (Eq. (12))                         */
+    double max_u;               /* max_x |u_eq|                                               */
+    double du;                  /* delta u since the previous observation (Sec. IV)           */
+    double dP_rel_change;       /* |dP - dP_prev| / |dP_prev| since the previous observation  */
+    long long steps;            /* time steps taken since the last initialisation             */
+    unsigned status_bits;
+    int criterion;
+} lbm_obs;
+
+/* ---------------------------------------------------------------- set-up */
+
+/* Bytes of device workspace one lattice needs (two population buffers of
+ * 19 planes, a velocity snapshot for delta u, reduction scratch).  Returns 0
+ * for invalid arguments. */
+size_t lbm_workspace_bytes(lbm_box box, int stencil, int prec);
+
+/* Create a context for one periodic lattice (Sec. II).  tau: BGK relaxation
+ * time of Eq. (4), > 1/2.  G: coupling of Eq. (8); for the two closed-form psi
+ * kinds it must be below the critical coupling (-e^2 for exp(-1/n), -4 for
+ * 1 - exp(-n); Sec. II below Eq. (10), Sec. IV), else LBM_EINVAL.  Box sides
+ * must be >= 3 (E4) or >= 5 (E6/E8).  dev_workspace: caller-owned device
+ * memory of at least lbm_workspace_bytes bytes, else LBM_ENOMEM.
+ * cuda_stream: cudaStream_t used for all work.  *out receives a host-side
+ * context (free it with lbm_destroy).  The field is uninitialised until one of
+ * the lbm_init_* / lbm_set_populations calls. */
+lbm_status lbm_create(lbm_box box, double tau, double G, lbm_eos eos, int stencil, int prec,
+                      void* dev_workspace, size_t bytes, void* cuda_stream, lbm_ctx** out);
+
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Initialise a droplet (rho_in > rho_out) or bubble (rho_in < rho_out), Sec. IV
+ * Eq. (23): n(r) = (rho_in + rho_out)/2 - (rho_in - rho_out)/2 tanh((r - R)/width),
+ * r the minimum-image distance to center[3] = (x, y, z) (host array of 3), fluid at
+ * rest: f_i = f_i^eq(n, u = 0) (Eq. (6)).  width = 1 is the paper's profile.
+ * Resets the step counter and the convergence history.  Async. */
+lbm_status lbm_init_drop(lbm_ctx* ctx, const double center[3], double R,
+                         double rho_in, double rho_out, double width);
+
+/* Initialise from a host density field (nx*ny*nz doubles, layout above), fluid at
+ * rest.  The field is copied to the device inside the call (the host buffer may be
+ * reused on return).  For shifted storage the shift n0 is the field's mean. */
+lbm_status lbm_init_rho(lbm_ctx* ctx, const double* host_rho);
+
+/* Set / get the pre-collision populations f_i(x, t) of Eq. (3) from / to a host
+ * buffer of 19*nx*ny*nz doubles (layout above).  set resets the step counter; for
+ * shifted storage the shift n0 is the field's mean density.  get synchronises. */
+lbm_status lbm_set_populations(lbm_ctx* ctx, const double* host_f);
+lbm_status lbm_get_populations(lbm_ctx* ctx, double* host_f);
+
+/* ---------------------------------------------------------------- time stepping */
+
+/* Advance n >= 0 time steps of Eq. (3) (collision Eqs. (4)-(8), then streaming).
+ * Async on the context stream; repeated calls replay a captured CUDA graph. */
+lbm_status lbm_step(lbm_ctx* ctx, long long n);
+
+/* Sec. IV convergence loop: every check_every steps (the paper uses 2^11) compare
+ * Delta P and the velocity field with the previous check; stop when
+ * |dP(t) - dP(t - check)| / |dP(t - check)| < tol_dP_rel (paper 1e-5) or
+ * delta u < tol_du (paper 1e-12), or after max_steps (LBM_ENOTCONV).  Writes the
+ * steps taken and the criterion that fired (0/1/2) when the pointers are non-null.
+ * Synchronises once per check. */
+lbm_status lbm_run_to_convergence(lbm_ctx* ctx, long long max_steps, long long check_every,
+                                  double tol_dP_rel, double tol_du,
+                                  long long* steps_done, int* criterion);
+
+/* ---------------------------------------------------------------- observables */
+
+/* Measure all observables of the current field (FP64 reductions on the device)
+ * and copy them to *out.  du and dP_rel_change compare with the previous call
+ * (or the previous convergence check); the first call after an init reports 0
+ * and NaN.  Synchronises.  Returns LBM_OK even when status_bits are set; the
+ * result statuses are in out->status_bits. */
+lbm_status lbm_observables(lbm_ctx* ctx, lbm_obs* out);
+
+/* Density n(c + r e_x) and tangential pressure P_T(r) = P^yy(c + r e_x) of
+ * Eq. (9) along the +x half axis, r = 0..nx/2 (Sec. III below Eq. (22)).  len
+ * must be nx/2 + 1.  Valid after lbm_observables.  Synchronises. */
+lbm_status lbm_rho_profile(lbm_ctx* ctx, double* host_out, long long len);
+lbm_status lbm_pt_profile(lbm_ctx* ctx, double* host_out, long long len);
+
+/* Generalised surface tension sigma[R] (Eq. (21)) and its notional derivative
+ * [dsigma/dR] (Eq. (22)) at m host radii R[k] > 0, from the last lbm_observables:
+ * sigma = dP R/3 + C/R^2 and dsigma = dP/3 - 2C/R^3 + 2D/R^2 (the step P_J
+ * integrated exactly, P_T by the trapezoid rule on the nodes).  Host arrays. */
+lbm_status lbm_sigma_of_R(lbm_ctx* ctx, const double* R, double* sigma, double* dsigma,
+                          long long m);
+
+/* Copy the density field n(x) (nx*ny*nz doubles) / the Guo velocity u_eq of
+ * Eq. (7) (3 planes of nx*ny*nz doubles: x, y, z components) to the host.
+ * Synchronises. */
+lbm_status lbm_copy_rho(lbm_ctx* ctx, double* host_out);
+lbm_status lbm_copy_velocity(lbm_ctx* ctx, double* host_out);
+
+/* Checkpoint: raw populations + step counter + shift/scale, to / from a file.  A
+ * load requires the same box, precision and stencil.  Synchronises. */
+lbm_status lbm_save(lbm_ctx* ctx, const char* path);
+lbm_status lbm_load(lbm_ctx* ctx, const char* path);
+
+/* Choose the step kernel's tile shape and z-chunk for this context by timing
+ * candidates on the current field (which it advances by an even number of steps
+ * and then restores).  Optional; lbm_create starts from a size-based default.
+ * Synchronises.  *choice (may be null) receives bx*1000000 + by*10000 + zchunk. */
+lbm_status lbm_autotune(lbm_ctx* ctx, int reps, long long* choice);
+
+/* Shift n0 and storage scale of the populations (F32/F16 modes; 0 and 1 for F64). */
+lbm_status lbm_storage_params(const lbm_ctx* ctx, double* n0, double* scale);
+
+const char* lbm_strerror(lbm_status s);
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* ---------------------------------------------------------------- Tolman fit */
+
+/* Least-squares fit of Eq. (2) / Eq. (12): sigma_s = sigma0 (1 - 2 delta x + c x^2)
+ * with x = 1/R_s, negative for bubbles (Sec. IV: bubbles have negative curvature).
+ * Host arrays of m entries; entries with non-finite R_s or sigma_s are skipped.
+ * quadratic = 0 fits the line (c = 0).  Host-only; needs >= 2 (3) usable points. */
+lbm_status lbm_tolman_fit(const double* R_s, const double* sigma_s, const int* is_bubble,
+                          long long m, int quadratic, double* sigma0, double* delta, double* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

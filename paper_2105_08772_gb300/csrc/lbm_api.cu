@@ -1,0 +1,763 @@
+// C ABI of liblbm.so (declarations and contracts in include/lbm.h).
+//
+// Host side of one lattice: workspace carving, argument checks, the
+// step loop replayed from captured CUDA graphs, the observable pipeline
+// (point pass -> field pass -> finalize, all on the context stream), the
+// convergence loop of Sec. IV, population transfer, checkpoints, the tile
+// autotuner and the Tolman least-squares fit.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_launch.h"
+
+using namespace lbm;
+
+struct lbm_ctx {
+  lbm_box box;
+  double tau, G;
+  lbm_eos eos;
+  int stencil, prec;
+  cudaStream_t stream;        // caller's stream (all work)
+  cudaStream_t cap_stream;    // private stream used only to capture graphs
+  char* ws;
+  size_t ws_bytes;
+  void* pop[2];
+  void* u_old;
+  FieldPartial* partials;
+  long long max_partials;
+  PointOut* pts;
+  double* dP_prev;
+  lbm_obs* obs_dev;
+  double* n_line;
+  double* PT_line;
+  int line_len;
+  int cur;                    // buffer holding the current state
+  long long steps;
+  int have_u_old;
+  int initialised;
+  double contrast0;
+  double n0, scale;
+  TileCfg step_cfg;
+  int obs_zchunk;
+  cudaGraphExec_t graph[2];   // graph_len steps, captured from parity 0 / 1
+  int graph_len;
+  lbm_obs last;
+  int have_last;
+  char err[512];
+};
+
+namespace {
+
+thread_local char g_err[512];
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const char* fmt, ...) {
+  char* buf = c ? c->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define LBM_CUDA(ctx, call)                                                              \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail((ctx), LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+  } while (0)
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t storage_bytes(int prec) { return prec == kF64 ? 8 : (prec == kF32 ? 4 : 2); }
+
+int radius_of(int stencil) { return stencil == 4 ? 1 : 2; }
+
+bool valid_stencil(int s) { return s == 4 || s == 6 || s == 8; }
+bool valid_prec(int p) { return p == kF64 || p == kF32 || p == kF16; }
+
+constexpr int kObsBX = 32, kObsBY = 4;
+
+int default_obs_zchunk(lbm_box b) { return b.nz < 8 ? b.nz : 8; }
+
+long long obs_partials(lbm_box b, int zchunk) {
+  return (long long)((b.nx + kObsBX - 1) / kObsBX) * ((b.ny + kObsBY - 1) / kObsBY) *
+         ((b.nz + zchunk - 1) / zchunk);
+}
+
+struct Layout {
+  size_t pop, u_old, partials, state, lines, total;
+  long long npart;
+};
+
+Layout layout_of(lbm_box b, int prec) {
+  Layout L;
+  const size_t N = (size_t)b.nx * b.ny * b.nz;
+  L.npart = obs_partials(b, default_obs_zchunk(b));
+  L.pop = align256((size_t)Q * N * storage_bytes(prec));
+  L.u_old = align256(3 * N * (prec == kF64 ? 8 : 4));
+  L.partials = align256((size_t)L.npart * sizeof(FieldPartial));
+  L.state = align256(sizeof(PointOut) + sizeof(double) + sizeof(lbm_obs) + 64);
+  L.lines = align256(2 * sizeof(double) * (size_t)(b.nx / 2 + 1));
+  L.total = 2 * L.pop + L.u_old + L.partials + L.state + L.lines;
+  return L;
+}
+
+bool box_ok(lbm_box b, int stencil) {
+  const int m = 2 * radius_of(stencil) + 1;
+  if (b.nx < m || b.ny < m || b.nz < m) return false;
+  const double n = (double)b.nx * b.ny * b.nz;
+  return n * Q < 9.0e18 && b.nx <= (1 << 20) && b.ny <= (1 << 20) && b.nz <= (1 << 20);
+}
+
+LatticeDesc desc_of(const lbm_ctx* c, int src_buf) {
+  LatticeDesc d;
+  d.src = c->pop[src_buf];
+  d.dst = c->pop[src_buf ^ 1];
+  d.nx = c->box.nx;
+  d.ny = c->box.ny;
+  d.nz = c->box.nz;
+  d.plane = (long long)c->box.nx * c->box.ny * c->box.nz;
+  d.omega = 1.0 / c->tau;
+  d.n0 = c->n0;
+  d.scale = c->scale;
+  d.eos.kind = c->eos.kind;
+  d.eos.G = c->G;
+  d.eos.a = c->eos.a;
+  d.eos.b = c->eos.b;
+  d.eos.Rgas = c->eos.Rgas;
+  d.eos.T = c->eos.T;
+  return d;
+}
+
+TileCfg default_tile(lbm_box b, int prec, int stencil) {
+  TileCfg t;
+  t.bx = 32;
+  t.by = (prec == kF64 || stencil != 4) ? 4 : 8;
+  t.zchunk = b.nz < 16 ? b.nz : 16;
+  return t;
+}
+
+void drop_graphs(lbm_ctx* c) {
+  for (int p = 0; p < 2; ++p) {
+    if (c->graph[p]) cudaGraphExecDestroy(c->graph[p]);
+    c->graph[p] = nullptr;
+  }
+}
+
+lbm_status prepare_kernels(lbm_ctx* c) {
+  // set the dynamic shared-memory limit of every kernel this context can use,
+  // outside any stream capture
+  LatticeDesc d = desc_of(c, 0);
+  ObsArgs oa{};
+  const int (*shapes)[2] = c->stencil == 4 ? kShapesE4 : kShapesWide;
+  const int ns = c->stencil == 4 ? kNumShapesE4 : kNumShapesWide;
+  for (int k = 0; k < ns; ++k) {
+    TileCfg t{shapes[k][0], shapes[k][1], 0};
+    LBM_CUDA(c, launch_lattice(c->prec, c->stencil, kModeStep, d, t, oa, c->stream));
+  }
+  TileCfg t{kObsBX, kObsBY, 0};
+  LBM_CUDA(c, launch_lattice(c->prec, c->stencil, kModeObs, d, t, oa, c->stream));
+  return LBM_OK;
+}
+
+lbm_status launch_steps_eager(lbm_ctx* c, long long n, cudaStream_t s) {
+  ObsArgs oa{};
+  for (long long k = 0; k < n; ++k) {
+    LatticeDesc d = desc_of(c, c->cur);
+    LBM_CUDA(c, launch_lattice(c->prec, c->stencil, kModeStep, d, c->step_cfg, oa, s));
+    c->cur ^= 1;
+  }
+  return LBM_OK;
+}
+
+lbm_status ensure_graph(lbm_ctx* c) {
+  const int p = c->cur;
+  if (c->graph[p]) return LBM_OK;
+  cudaGraph_t g = nullptr;
+  LBM_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const int cur0 = c->cur;
+  lbm_status st = launch_steps_eager(c, c->graph_len, c->cap_stream);
+  c->cur = cur0;   // graph_len is even; capture does not advance the state
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (st != LBM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(c, LBM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->graph[p], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph[p] = nullptr;
+    return fail(c, LBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  }
+  return LBM_OK;
+}
+
+lbm_status observe(lbm_ctx* c, double* rho_out, double* u_out, int write_u_old, bool finalize) {
+  LatticeDesc d = desc_of(c, c->cur);
+  LBM_CUDA(c, launch_point_obs(c->prec, c->stencil, d, c->pts, c->n_line, c->PT_line, c->stream));
+  ObsArgs oa;
+  oa.n_out = &c->pts->n_out;
+  oa.u_old = c->u_old;
+  oa.have_u_old = c->have_u_old;
+  oa.partials = c->partials;
+  oa.rho_out = rho_out;
+  oa.u_out = u_out;
+  oa.write_u_old = write_u_old;
+  TileCfg t{kObsBX, kObsBY, c->obs_zchunk};
+  LBM_CUDA(c, launch_lattice(c->prec, c->stencil, kModeObs, d, t, oa, c->stream));
+  if (finalize) {
+    FinalizeArgs fa;
+    fa.partials = c->partials;
+    fa.n_partials = lattice_grid_ctas(d, t);
+    fa.pts = c->pts;
+    fa.PT_line = c->PT_line;
+    fa.line_len = c->line_len;
+    fa.volume = d.plane;
+    fa.contrast0 = c->contrast0;
+    fa.center[0] = c->box.nx / 2;
+    fa.center[1] = c->box.ny / 2;
+    fa.center[2] = c->box.nz / 2;
+    fa.have_u_old = c->have_u_old;
+    fa.steps = c->steps;
+    fa.dP_prev = c->dP_prev;
+    fa.obs_out = c->obs_dev;
+    LBM_CUDA(c, launch_finalize(fa, c->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status reset_history(lbm_ctx* c) {
+  const double nan = NAN;
+  LBM_CUDA(c, cudaMemcpyAsync(c->dP_prev, &nan, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->have_u_old = 0;
+  c->have_last = 0;
+  c->steps = 0;
+  c->initialised = 1;
+  return LBM_OK;
+}
+
+void choose_storage(lbm_ctx* c, double n0, double maxdev) {
+  if (c->prec == kF64) {
+    c->n0 = 0.0;
+    c->scale = 1.0;
+    return;
+  }
+  c->n0 = n0;
+  c->scale = 1.0;
+  if (c->prec == kF16) {
+    // power of two putting the largest expected |f_i - w_i n0| near 2^13
+    // (half's largest normal number is 65504)
+    const double m = maxdev > 0 ? maxdev : 1.0;
+    int k = (int)floor(log2(8192.0 / m));
+    if (k > 24) k = 24;
+    if (k < -24) k = -24;
+    c->scale = ldexp(1.0, k);
+  }
+}
+
+double* temp_doubles(lbm_ctx* c) { return static_cast<double*>(c->pop[c->cur ^ 1]); }
+
+#define LBM_CHECK_CTX(c)                                                  \
+  do {                                                                    \
+    if (!(c)) return fail(nullptr, LBM_EINVAL, "null context");           \
+  } while (0)
+#define LBM_CHECK_INIT(c)                                                                   \
+  do {                                                                                      \
+    if (!(c)->initialised) return fail((c), LBM_EINVAL, "field not initialised");          \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_workspace_bytes(lbm_box box, int stencil, int prec) {
+  if (!valid_stencil(stencil) || !valid_prec(prec) || !box_ok(box, stencil)) return 0;
+  return layout_of(box, prec).total;
+}
+
+lbm_status lbm_create(lbm_box box, double tau, double G, lbm_eos eos, int stencil, int prec,
+                      void* dev_workspace, size_t bytes, void* cuda_stream, lbm_ctx** out) {
+  if (!out) return fail(nullptr, LBM_EINVAL, "out is null");
+  *out = nullptr;
+  if (!valid_stencil(stencil)) return fail(nullptr, LBM_EINVAL, "stencil must be 4, 6 or 8");
+  if (!valid_prec(prec)) return fail(nullptr, LBM_EINVAL, "prec must be 0, 1 or 2");
+  if (!box_ok(box, stencil))
+    return fail(nullptr, LBM_EINVAL, "box %dx%dx%d too small (sides >= %d)", box.nx, box.ny, box.nz,
+                2 * radius_of(stencil) + 1);
+  if (!(tau > 0.5) || !isfinite(tau)) return fail(nullptr, LBM_EINVAL, "tau must be > 1/2");
+  if (!isfinite(G)) return fail(nullptr, LBM_EINVAL, "G must be finite");
+  if (eos.kind == LBM_PSI_EXP_INV) {
+    const double Gc = -exp(2.0);   // psi = exp(-1/n): n_c = 1, G_c = -e^2
+    if (!(G < Gc))
+      return fail(nullptr, LBM_EINVAL, "G = %g is not below G_c = %.6f for psi = exp(-1/n): no coexistence",
+                  G, Gc);
+  } else if (eos.kind == LBM_PSI_ONE_MINUS_EXP) {
+    if (!(G < -4.0))
+      return fail(nullptr, LBM_EINVAL, "G = %g is not below G_c = -4 for psi = 1 - exp(-n): no coexistence", G);
+  } else if (eos.kind == LBM_PSI_CS) {
+    if (!(G < 0) || !(eos.T > 0) || !(eos.a > 0) || !(eos.b > 0) || !(eos.Rgas > 0))
+      return fail(nullptr, LBM_EINVAL, "Carnahan-Starling psi needs G < 0 and a, b, Rgas, T > 0");
+  } else {
+    return fail(nullptr, LBM_EINVAL, "unknown psi kind %d", eos.kind);
+  }
+  const Layout L = layout_of(box, prec);
+  if (!dev_workspace) return fail(nullptr, LBM_EINVAL, "workspace is null");
+  if (((uintptr_t)dev_workspace & 255) != 0) return fail(nullptr, LBM_EINVAL, "workspace not 256-byte aligned");
+  if (bytes < L.total)
+    return fail(nullptr, LBM_ENOMEM, "workspace has %zu bytes, needs %zu", bytes, L.total);
+
+  lbm_ctx* c = new lbm_ctx();
+  memset(c->err, 0, sizeof(c->err));
+  c->box = box;
+  c->tau = tau;
+  c->G = G;
+  c->eos = eos;
+  c->stencil = stencil;
+  c->prec = prec;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->ws = static_cast<char*>(dev_workspace);
+  c->ws_bytes = bytes;
+  char* p = c->ws;
+  c->pop[0] = p; p += L.pop;
+  c->pop[1] = p; p += L.pop;
+  c->u_old = p; p += L.u_old;
+  c->partials = reinterpret_cast<FieldPartial*>(p); p += L.partials;
+  c->max_partials = L.npart;
+  c->pts = reinterpret_cast<PointOut*>(p);
+  c->dP_prev = reinterpret_cast<double*>(p + 64);
+  c->obs_dev = reinterpret_cast<lbm_obs*>(p + 128);
+  p += L.state;
+  c->line_len = box.nx / 2 + 1;
+  c->n_line = reinterpret_cast<double*>(p);
+  c->PT_line = c->n_line + c->line_len;
+  c->cur = 0;
+  c->n0 = 0.0;
+  c->scale = 1.0;
+  c->step_cfg = default_tile(box, prec, stencil);
+  c->obs_zchunk = default_obs_zchunk(box);
+  c->graph[0] = c->graph[1] = nullptr;
+  c->graph_len = 128;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, LBM_ECUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(e));
+  }
+  lbm_status st = prepare_kernels(c);
+  if (st != LBM_OK) {
+    snprintf(g_err, sizeof(g_err), "%s", c->err);
+    cudaStreamDestroy(c->cap_stream);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  drop_graphs(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+lbm_status lbm_init_drop(lbm_ctx* c, const double center[3], double R, double rho_in,
+                         double rho_out, double width) {
+  LBM_CHECK_CTX(c);
+  if (!center) return fail(c, LBM_EINVAL, "center is null");
+  if (!(R > 0) || !(width > 0) || !(rho_in > 0) || !(rho_out > 0) || !isfinite(R) ||
+      !isfinite(rho_in) || !isfinite(rho_out) || !isfinite(width))
+    return fail(c, LBM_EINVAL, "R, width and densities must be positive and finite");
+  for (int k = 0; k < 3; ++k)
+    if (!isfinite(center[k])) return fail(c, LBM_EINVAL, "center must be finite");
+  choose_storage(c, 0.5 * (rho_in + rho_out), (1.0 / 3.0) * fabs(rho_in - rho_out));
+  c->cur = 0;
+  drop_graphs(c);
+  DropInit di{center[0], center[1], center[2], R, rho_in, rho_out, width};
+  LatticeDesc d = desc_of(c, 1);   // writes pop[0]
+  LBM_CUDA(c, launch_init_drop(c->prec, d, di, c->stream));
+  c->contrast0 = fabs(rho_in - rho_out);
+  return reset_history(c);
+}
+
+lbm_status lbm_init_rho(lbm_ctx* c, const double* host_rho) {
+  LBM_CHECK_CTX(c);
+  if (!host_rho) return fail(c, LBM_EINVAL, "host_rho is null");
+  const long long N = (long long)c->box.nx * c->box.ny * c->box.nz;
+  double mn = host_rho[0], mx = host_rho[0], sum = 0.0;
+  for (long long k = 0; k < N; ++k) {
+    const double v = host_rho[k];
+    if (!(v > 0) || !isfinite(v)) return fail(c, LBM_EINVAL, "density must be positive and finite");
+    mn = v < mn ? v : mn;
+    mx = v > mx ? v : mx;
+    sum += v;
+  }
+  const double mean = sum / (double)N;
+  choose_storage(c, mean, (1.0 / 3.0) * fmax(mx - mean, mean - mn));
+  c->cur = 0;
+  drop_graphs(c);
+  double* tmp = static_cast<double*>(c->pop[1]);
+  LBM_CUDA(c, cudaMemcpyAsync(tmp, host_rho, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  LatticeDesc d = desc_of(c, 1);   // writes pop[0]
+  LBM_CUDA(c, launch_init_rho(c->prec, d, tmp, c->stream));
+  c->contrast0 = mx - mn;
+  return reset_history(c);
+}
+
+lbm_status lbm_set_populations(lbm_ctx* c, const double* host_f) {
+  LBM_CHECK_CTX(c);
+  if (!host_f) return fail(c, LBM_EINVAL, "host_f is null");
+  const long long N = (long long)c->box.nx * c->box.ny * c->box.nz;
+  std::vector<double> n(N, 0.0);
+  for (int i = 0; i < Q; ++i)
+    for (long long k = 0; k < N; ++k) {
+      const double v = host_f[(long long)i * N + k];
+      if (!isfinite(v)) return fail(c, LBM_EINVAL, "populations must be finite");
+      n[k] += v;
+    }
+  double mn = n[0], mx = n[0], sum = 0.0;
+  for (long long k = 0; k < N; ++k) {
+    mn = n[k] < mn ? n[k] : mn;
+    mx = n[k] > mx ? n[k] : mx;
+    sum += n[k];
+  }
+  const double mean = sum / (double)N;
+  double maxdev = 0.0;
+  for (int i = 0; i < Q; ++i)
+    for (long long k = 0; k < N; ++k)
+      maxdev = fmax(maxdev, fabs(host_f[(long long)i * N + k] - wq(i) * mean));
+  choose_storage(c, mean, maxdev);
+  c->cur = 0;
+  drop_graphs(c);
+  double* tmp = static_cast<double*>(c->pop[1]);
+  LatticeDesc d = desc_of(c, 1);   // writes pop[0]
+  for (int i = 0; i < Q; ++i) {
+    LBM_CUDA(c, cudaMemcpyAsync(tmp, host_f + (long long)i * N, N * sizeof(double),
+                                cudaMemcpyHostToDevice, c->stream));
+    LBM_CUDA(c, launch_set_plane(c->prec, d, i, tmp, c->stream));
+  }
+  c->contrast0 = mx - mn;
+  return reset_history(c);
+}
+
+lbm_status lbm_get_populations(lbm_ctx* c, double* host_f) {
+  LBM_CHECK_CTX(c);
+  LBM_CHECK_INIT(c);
+  if (!host_f) return fail(c, LBM_EINVAL, "host_f is null");
+  const long long N = (long long)c->box.nx * c->box.ny * c->box.nz;
+  double* tmp = temp_doubles(c);
+  LatticeDesc d = desc_of(c, c->cur);
+  for (int i = 0; i < Q; ++i) {
+    LBM_CUDA(c, launch_get_plane(c->prec, d, i, tmp, c->stream));
+    LBM_CUDA(c, cudaMemcpyAsync(host_f + (long long)i * N, tmp, N * sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+  }
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, long long n) {
+  LBM_CHECK_CTX(c);
+  LBM_CHECK_INIT(c);
+  if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
+  while (n >= c->graph_len) {
+    lbm_status st = ensure_graph(c);
+    if (st != LBM_OK) return st;
+    LBM_CUDA(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+    n -= c->graph_len;
+    c->steps += c->graph_len;
+  }
+  lbm_status st = launch_steps_eager(c, n, c->stream);
+  if (st != LBM_OK) return st;
+  c->steps += n;
+  return LBM_OK;
+}
+
+lbm_status lbm_observables(lbm_ctx* c, lbm_obs* out) {
+  LBM_CHECK_CTX(c);
+  LBM_CHECK_INIT(c);
+  lbm_status st = observe(c, nullptr, nullptr, 1, true);
+  if (st != LBM_OK) return st;
+  LBM_CUDA(c, cudaMemcpyAsync(&c->last, c->obs_dev, sizeof(lbm_obs), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->have_u_old = 1;
+  c->have_last = 1;
+  if (out) *out = c->last;
+  return LBM_OK;
+}
+
+lbm_status lbm_run_to_convergence(lbm_ctx* c, long long max_steps, long long check_every,
+                                  double tol_dP_rel, double tol_du, long long* steps_done,
+                                  int* criterion) {
+  LBM_CHECK_CTX(c);
+  LBM_CHECK_INIT(c);
+  if (max_steps < 0 || check_every < 1) return fail(c, LBM_EINVAL, "max_steps >= 0, check_every >= 1");
+  lbm_status st;
+  if (!c->have_last) {
+    st = lbm_observables(c, nullptr);
+    if (st != LBM_OK) return st;
+  }
+  long long done = 0;
+  int crit = 0;
+  while (done < max_steps) {
+    const long long k = (max_steps - done < check_every) ? max_steps - done : check_every;
+    st = lbm_step(c, k);
+    if (st != LBM_OK) return st;
+    done += k;
+    st = lbm_observables(c, nullptr);
+    if (st != LBM_OK) return st;
+    if (c->last.status_bits & 8u) {
+      if (steps_done) *steps_done = done;
+      if (criterion) *criterion = 0;
+      return fail(c, LBM_ENUMERIC, "non-finite or non-positive density after %lld steps", c->steps);
+    }
+    if (c->last.dP_rel_change < tol_dP_rel) { crit = 1; break; }
+    if (c->last.du < tol_du) { crit = 2; break; }
+  }
+  c->last.criterion = crit;
+  if (steps_done) *steps_done = done;
+  if (criterion) *criterion = crit;
+  if (!crit) return fail(c, LBM_ENOTCONV, "not converged after %lld steps", done);
+  return LBM_OK;
+}
+
+lbm_status lbm_rho_profile(lbm_ctx* c, double* host_out, long long len) {
+  LBM_CHECK_CTX(c);
+  if (!host_out || len != c->line_len) return fail(c, LBM_EINVAL, "len must be nx/2 + 1 = %d", c->line_len);
+  if (!c->have_last) return fail(c, LBM_EINVAL, "call lbm_observables first");
+  LBM_CUDA(c, cudaMemcpyAsync(host_out, c->n_line, len * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_pt_profile(lbm_ctx* c, double* host_out, long long len) {
+  LBM_CHECK_CTX(c);
+  if (!host_out || len != c->line_len) return fail(c, LBM_EINVAL, "len must be nx/2 + 1 = %d", c->line_len);
+  if (!c->have_last) return fail(c, LBM_EINVAL, "call lbm_observables first");
+  LBM_CUDA(c, cudaMemcpyAsync(host_out, c->PT_line, len * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_sigma_of_R(lbm_ctx* c, const double* R, double* sigma, double* dsigma, long long m) {
+  LBM_CHECK_CTX(c);
+  if (!c->have_last) return fail(c, LBM_EINVAL, "call lbm_observables first");
+  if (m < 0 || (m > 0 && (!R || !sigma || !dsigma))) return fail(c, LBM_EINVAL, "bad arrays");
+  const double dP = c->last.dP, C = c->last.C, D = c->last.D;
+  for (long long k = 0; k < m; ++k) {
+    if (!(R[k] > 0)) return fail(c, LBM_EINVAL, "R must be > 0");
+    const double r = R[k];
+    sigma[k] = dP * r / 3.0 + C / (r * r);
+    dsigma[k] = dP / 3.0 - 2.0 * C / (r * r * r) + 2.0 * D / (r * r);
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_copy_rho(lbm_ctx* c, double* host_out) {
+  LBM_CHECK_CTX(c);
+  LBM_CHECK_INIT(c);
+  if (!host_out) return fail(c, LBM_EINVAL, "host_out is null");
+  const long long N = (long long)c->box.nx * c->box.ny * c->box.nz;
+  double* tmp = temp_doubles(c);
+  lbm_status st = observe(c, tmp, nullptr, 0, false);
+  if (st != LBM_OK) return st;
+  LBM_CUDA(c, cudaMemcpyAsync(host_out, tmp, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_copy_velocity(lbm_ctx* c, double* host_out) {
+  LBM_CHECK_CTX(c);
+  LBM_CHECK_INIT(c);
+  if (!host_out) return fail(c, LBM_EINVAL, "host_out is null");
+  const long long N = (long long)c->box.nx * c->box.ny * c->box.nz;
+  double* tmp = temp_doubles(c);
+  lbm_status st = observe(c, nullptr, tmp, 0, false);
+  if (st != LBM_OK) return st;
+  LBM_CUDA(c, cudaMemcpyAsync(host_out, tmp, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+static const char kMagic[8] = {'L', 'B', 'M', 'G', 'B', '3', '0', '0'};
+
+struct CkptHeader {
+  char magic[8];
+  int version, nx, ny, nz, prec, stencil;
+  long long steps;
+  double n0, scale, contrast0;
+};
+
+lbm_status lbm_save(lbm_ctx* c, const char* path) {
+  LBM_CHECK_CTX(c);
+  LBM_CHECK_INIT(c);
+  if (!path) return fail(c, LBM_EINVAL, "path is null");
+  const size_t bytes = (size_t)Q * c->box.nx * c->box.ny * c->box.nz * storage_bytes(c->prec);
+  std::vector<char> buf(bytes);
+  LBM_CUDA(c, cudaMemcpyAsync(buf.data(), c->pop[c->cur], bytes, cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(c, LBM_EINVAL, "cannot open %s for writing", path);
+  CkptHeader h;
+  memcpy(h.magic, kMagic, 8);
+  h.version = 1;
+  h.nx = c->box.nx; h.ny = c->box.ny; h.nz = c->box.nz;
+  h.prec = c->prec; h.stencil = c->stencil;
+  h.steps = c->steps; h.n0 = c->n0; h.scale = c->scale; h.contrast0 = c->contrast0;
+  const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(buf.data(), 1, bytes, f) == bytes;
+  fclose(f);
+  if (!ok) return fail(c, LBM_EINVAL, "short write to %s", path);
+  return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_ctx* c, const char* path) {
+  LBM_CHECK_CTX(c);
+  if (!path) return fail(c, LBM_EINVAL, "path is null");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(c, LBM_EINVAL, "cannot open %s", path);
+  CkptHeader h;
+  if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) {
+    fclose(f);
+    return fail(c, LBM_EINVAL, "%s is not a checkpoint of this library", path);
+  }
+  if (h.nx != c->box.nx || h.ny != c->box.ny || h.nz != c->box.nz || h.prec != c->prec ||
+      h.stencil != c->stencil) {
+    fclose(f);
+    return fail(c, LBM_EINVAL, "checkpoint box/precision/stencil differ from the context");
+  }
+  const size_t bytes = (size_t)Q * c->box.nx * c->box.ny * c->box.nz * storage_bytes(c->prec);
+  std::vector<char> buf(bytes);
+  const bool ok = fread(buf.data(), 1, bytes, f) == bytes;
+  fclose(f);
+  if (!ok) return fail(c, LBM_EINVAL, "truncated checkpoint %s", path);
+  c->cur = 0;
+  drop_graphs(c);
+  LBM_CUDA(c, cudaMemcpyAsync(c->pop[0], buf.data(), bytes, cudaMemcpyHostToDevice, c->stream));
+  c->n0 = h.n0;
+  c->scale = h.scale;
+  c->contrast0 = h.contrast0;
+  lbm_status st = reset_history(c);
+  c->steps = h.steps;
+  return st;
+}
+
+lbm_status lbm_autotune(lbm_ctx* c, int reps, long long* choice) {
+  LBM_CHECK_CTX(c);
+  LBM_CHECK_INIT(c);
+  if (reps < 2) reps = 2;
+  reps += reps & 1;
+  const int (*shapes)[2] = c->stencil == 4 ? kShapesE4 : kShapesWide;
+  const int ns = c->stencil == 4 ? kNumShapesE4 : kNumShapesWide;
+  const int zcands[] = {4, 8, 16, 32, 64};
+  cudaEvent_t e0, e1;
+  LBM_CUDA(c, cudaEventCreate(&e0));
+  LBM_CUDA(c, cudaEventCreate(&e1));
+  TileCfg best = c->step_cfg;
+  float best_ms = 1e30f;
+  lbm_status st = LBM_OK;
+  for (int k = 0; k < ns && st == LBM_OK; ++k) {
+    for (int zc : zcands) {
+      if (zc > c->box.nz && zc != 4) continue;
+      TileCfg t{shapes[k][0], shapes[k][1], zc < c->box.nz ? zc : c->box.nz};
+      c->step_cfg = t;
+      st = launch_steps_eager(c, 2, c->stream);
+      if (st != LBM_OK) break;
+      cudaEventRecord(e0, c->stream);
+      st = launch_steps_eager(c, reps, c->stream);
+      if (st != LBM_OK) break;
+      cudaEventRecord(e1, c->stream);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) { st = fail(c, LBM_ECUDA, "autotune: %s", cudaGetErrorString(e)); break; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      c->steps += reps + 2;
+      if (ms < best_ms) { best_ms = ms; best = t; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->step_cfg = best;
+  drop_graphs(c);
+  c->have_u_old = 0;
+  if (st != LBM_OK) return st;
+  if (choice) *choice = (long long)best.bx * 1000000 + best.by * 10000 + best.zchunk;
+  return LBM_OK;
+}
+
+lbm_status lbm_storage_params(const lbm_ctx* c, double* n0, double* scale) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "null context");
+  if (n0) *n0 = c->n0;
+  if (scale) *scale = c->scale;
+  return LBM_OK;
+}
+
+const char* lbm_strerror(lbm_status s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "workspace too small";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_ENUMERIC: return "non-finite or non-positive density";
+    case LBM_ENOTCONV: return "not converged";
+    case LBM_ENOMIN: return "sigma[R] has no minimum";
+    case LBM_ECOLLAPSE: return "droplet/bubble collapsed";
+    case LBM_EOFFCENTER: return "centre of mass off centre";
+    case LBM_ETIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : g_err; }
+
+lbm_status lbm_tolman_fit(const double* R_s, const double* sigma_s, const int* is_bubble,
+                          long long m, int quadratic, double* sigma0, double* delta, double* cc) {
+  if (m < 0 || (m > 0 && (!R_s || !sigma_s || !is_bubble)) || !sigma0 || !delta || !cc)
+    return fail(nullptr, LBM_EINVAL, "bad arguments");
+  const int np = quadratic ? 3 : 2;
+  // normal equations A^T A a = A^T s with rows (1, x, x^2), x = +-1/R_s
+  double M[3][3] = {{0}}, v[3] = {0};
+  long long used = 0;
+  for (long long k = 0; k < m; ++k) {
+    if (!isfinite(R_s[k]) || !isfinite(sigma_s[k]) || R_s[k] == 0.0) continue;
+    const double x = (is_bubble[k] ? -1.0 : 1.0) / R_s[k];
+    const double row[3] = {1.0, x, x * x};
+    for (int i = 0; i < np; ++i) {
+      v[i] += row[i] * sigma_s[k];
+      for (int j = 0; j < np; ++j) M[i][j] += row[i] * row[j];
+    }
+    ++used;
+  }
+  if (used < np) return fail(nullptr, LBM_EINVAL, "need at least %d usable points, have %lld", np, used);
+  // Gauss-Jordan with partial pivoting
+  double a[3] = {0, 0, 0};
+  for (int col = 0; col < np; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < np; ++r)
+      if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
+    if (M[piv][col] == 0.0) return fail(nullptr, LBM_EINVAL, "singular fit");
+    if (piv != col) {
+      for (int j = 0; j < np; ++j) { double t = M[col][j]; M[col][j] = M[piv][j]; M[piv][j] = t; }
+      double t = v[col]; v[col] = v[piv]; v[piv] = t;
+    }
+    for (int r = 0; r < np; ++r) {
+      if (r == col) continue;
+      const double f = M[r][col] / M[col][col];
+      for (int j = 0; j < np; ++j) M[r][j] -= f * M[col][j];
+      v[r] -= f * v[col];
+    }
+  }
+  for (int i = 0; i < np; ++i) a[i] = v[i] / M[i][i];
+  *sigma0 = a[0];
+  *delta = -a[1] / (2.0 * a[0]);
+  *cc = quadratic ? a[2] / a[0] : 0.0;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// Shared device definitions of the GB300 Shan-Chen LBM library.
+//
+// D3Q19 velocity set and weights (Sec. II; c_s^2 = 1/3), the forcing
+// stencils of Eq. (8), the pseudopotentials psi(n) and the storage
+// precisions.  The population order is the one documented in include/lbm.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// velocity components, population order of include/lbm.h
+__host__ __device__ constexpr int cx(int i) {
+  constexpr int t[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+  return t[i];
+}
+__host__ __device__ constexpr int cy(int i) {
+  constexpr int t[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+  return t[i];
+}
+__host__ __device__ constexpr int cz(int i) {
+  constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+  return t[i];
+}
+// D3Q19 weights: 1/3 rest, 1/18 axis, 1/36 diagonal
+__host__ __device__ constexpr double wq(int i) {
+  return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// ---------------------------------------------------------------- stencils
+// Forcing-stencil vectors, grouped by shell |xi|^2, with the shell weights
+// W(|xi|^2) that make the stencil isotropic to 4th (E4), 6th (E6) and 8th
+// (E8) order with e_2 = 1.  E4: W(1) = 1/6, W(2) = 1/12 (Sec. II).
+struct StencilVec { int8_t x, y, z; };
+
+constexpr int kE4Count = 18;
+constexpr int kE6Count = 32;
+constexpr int kE8Count = 92;
+
+enum PsiKind : int { kPsiExpInv = 0, kPsiOneMinusExp = 1, kPsiCS = 2 };
+
+struct EosParams {
+  int kind;
+  double G;       // coupling (Eq. (8))
+  double a, b, Rgas, T;  // Carnahan-Starling constants (kind == kPsiCS)
+};
+
+template <typename T>
+__device__ __forceinline__ T psi_of(T n, const EosParams& e);
+
+template <>
+__device__ __forceinline__ double psi_of<double>(double n, const EosParams& e) {
+  if (e.kind == kPsiOneMinusExp) return -expm1(-n);
+  if (e.kind == kPsiExpInv) return exp(-1.0 / n);
+  // Carnahan-Starling mapped: psi = sqrt(2 (p_CS - n c_s^2) / (G c_s^2))
+  const double q = e.b * n * 0.25;
+  const double om = 1.0 - q;
+  const double p = n * e.Rgas * e.T * (1.0 + q + q * q - q * q * q) / (om * om * om) - e.a * n * n;
+  return sqrt(2.0 * (p - n * (1.0 / 3.0)) / (e.G * (1.0 / 3.0)));
+}
+
+template <>
+__device__ __forceinline__ float psi_of<float>(float n, const EosParams& e) {
+  if (e.kind == kPsiOneMinusExp) return -expm1f(-n);
+  if (e.kind == kPsiExpInv) return expf(-1.0f / n);
+  const float q = (float)e.b * n * 0.25f;
+  const float om = 1.0f - q;
+  const float p = n * (float)(e.Rgas * e.T) * (1.0f + q + q * q - q * q * q) / (om * om * om) -
+                  (float)e.a * n * n;
+  return sqrtf(2.0f * (p - n * (1.0f / 3.0f)) / ((float)e.G * (1.0f / 3.0f)));
+}
+
+// ---------------------------------------------------------------- storage
+enum Prec : int { kF64 = 0, kF32 = 1, kF16 = 2 };
+
+template <int P> struct Storage;
+template <> struct Storage<kF64> {
+  using S = double;   // stored type
+  using T = double;   // arithmetic type
+  static __device__ __forceinline__ T load(const S* p, T /*inv_scale*/) { return __ldg(p); }
+  static __device__ __forceinline__ void store(S* p, T v, T /*scale*/) { *p = v; }
+};
+template <> struct Storage<kF32> {
+  using S = float;
+  using T = float;
+  static __device__ __forceinline__ T load(const S* p, T) { return __ldg(p); }
+  static __device__ __forceinline__ void store(S* p, T v, T) { *p = v; }
+};
+template <> struct Storage<kF16> {
+  using S = __half;
+  using T = float;
+  static __device__ __forceinline__ T load(const S* p, T inv_scale) {
+    return __half2float(__ldg(p)) * inv_scale;
+  }
+  static __device__ __forceinline__ void store(S* p, T v, T scale) {
+    *p = __float2half_rn(v * scale);
+  }
+};
+
+// One lattice as the kernels see it.  Populations are stored post-collision
+// and pre-streaming: slot i of node x holds f*_i(x, t-1), so the
+// pre-collision f_i(x, t) of Eq. (3) is slot i of node x - xi_i.
+struct LatticeDesc {
+  const void* src;      // populations read this step (19 planes)
+  void* dst;            // populations written this step
+  int nx, ny, nz;
+  long long plane;      // nx*ny*nz
+  double omega;         // 1/tau
+  double n0;            // storage shift (0 for F64)
+  double scale;         // storage scale (1 for F64/F32)
+  EosParams eos;
+};
+
+__host__ __device__ __forceinline__ int wrap(int g, int n) {
+  return g < 0 ? g + n : (g >= n ? g - n : g);
+}
+
+}  // namespace lbm

@@ -1,0 +1,9 @@
+// Lattice kernels (fused step + field observables) with f32 population storage.
+#include "lbm_lattice_inst.cuh"
+
+namespace lbm {
+cudaError_t launch_lattice_f32(int stencil, int mode, const LatticeDesc& d, TileCfg cfg,
+                               const ObsArgs& oa, cudaStream_t s) {
+  return dispatch_lattice<kF32>(stencil, mode, d, cfg, oa, s);
+}
+}  // namespace lbm

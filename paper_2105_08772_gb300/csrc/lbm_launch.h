@@ -1,0 +1,85 @@
+// Host-side launch interface between the C-ABI (lbm_api.cu) and the kernel
+// translation units (one per storage precision).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_common.cuh"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+struct TileCfg {
+  int bx, by, zchunk;
+};
+
+// tile shapes compiled for the step kernel (E4 / wider stencils)
+constexpr int kNumShapesE4 = 3;
+constexpr int kShapesE4[kNumShapesE4][2] = {{32, 4}, {32, 8}, {64, 4}};
+constexpr int kNumShapesWide = 2;
+constexpr int kShapesWide[kNumShapesWide][2] = {{32, 4}, {32, 8}};
+
+// Launch one step (mode kModeStep) or the field-observable pass (kModeObs)
+// for a lattice of the given precision and stencil.  Returns
+// cudaErrorInvalidValue for a shape that is not compiled.  cfg.zchunk == 0
+// launches nothing and only sets the kernel's shared-memory limit.
+cudaError_t launch_lattice_f64(int stencil, int mode, const LatticeDesc& d, TileCfg cfg,
+                               const ObsArgs& oa, cudaStream_t s);
+cudaError_t launch_lattice_f32(int stencil, int mode, const LatticeDesc& d, TileCfg cfg,
+                               const ObsArgs& oa, cudaStream_t s);
+cudaError_t launch_lattice_f16(int stencil, int mode, const LatticeDesc& d, TileCfg cfg,
+                               const ObsArgs& oa, cudaStream_t s);
+
+inline cudaError_t launch_lattice(int prec, int stencil, int mode, const LatticeDesc& d,
+                                  TileCfg cfg, const ObsArgs& oa, cudaStream_t s) {
+  switch (prec) {
+    case kF64: return launch_lattice_f64(stencil, mode, d, cfg, oa, s);
+    case kF32: return launch_lattice_f32(stencil, mode, d, cfg, oa, s);
+    case kF16: return launch_lattice_f16(stencil, mode, d, cfg, oa, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// number of CTAs (= FieldPartial records) a lattice launch uses
+inline long long lattice_grid_ctas(const LatticeDesc& d, TileCfg cfg) {
+  const long long tiles = (long long)((d.nx + cfg.bx - 1) / cfg.bx) * ((d.ny + cfg.by - 1) / cfg.by);
+  return tiles * ((d.nz + cfg.zchunk - 1) / cfg.zchunk);
+}
+
+// ---------------------------------------------------------------- io / init (lbm_io.cu)
+struct DropInit {
+  double cx, cy, cz, R, rho_in, rho_out, width;
+};
+cudaError_t launch_init_drop(int prec, const LatticeDesc& d, const DropInit& di, cudaStream_t s);
+cudaError_t launch_init_rho(int prec, const LatticeDesc& d, const double* rho_dev, cudaStream_t s);
+// write population plane i of the stored state from f_i(x, t) (device doubles)
+cudaError_t launch_set_plane(int prec, const LatticeDesc& d, int i, const double* f_dev,
+                             cudaStream_t s);
+// read population plane i of the current f_i(x, t) into device doubles
+cudaError_t launch_get_plane(int prec, const LatticeDesc& d, int i, double* f_dev, cudaStream_t s);
+
+// ---------------------------------------------------------------- observables (lbm_obs.cu)
+struct PointOut {
+  double n_in, n_out, P_in, P_out;
+};
+// centre node, farthest corner and the +x half axis: n, P^xx, P^yy (Eq. (9))
+cudaError_t launch_point_obs(int prec, int stencil, const LatticeDesc& d, PointOut* pts,
+                             double* n_line, double* PT_line, cudaStream_t s);
+
+struct FinalizeArgs {
+  const FieldPartial* partials;
+  long long n_partials;
+  const PointOut* pts;
+  const double* PT_line;
+  int line_len;
+  long long volume;
+  double contrast0;       // |rho_in - rho_out| of the initial state (0: no collapse test)
+  int center[3];          // centre node (nx/2, ny/2, nz/2)
+  int have_u_old;
+  long long steps;
+  double* dP_prev;        // device: previous Delta P (NaN if none); updated
+  void* obs_out;          // device lbm_obs
+};
+cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+
+}  // namespace lbm

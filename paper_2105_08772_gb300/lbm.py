@@ -1,0 +1,253 @@
+"""Python binding of the C ABI with the same names (argument marshalling only).
+
+Device memory and streams come from PyTorch: ``Lattice`` allocates the
+workspace as a uint8 CUDA tensor and passes its pointer and the current CUDA
+stream to ``lbm_create``.  Host buffers are numpy float64 arrays.  All of the
+method runs inside liblbm.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import (LBM_F16_SHIFTED, LBM_F32_SHIFTED, LBM_F64, PRECS, PSI_KINDS, STENCILS,
+                   LBMError, check, lbm_box, lbm_eos, lbm_obs)
+
+_lib_ = _lib.lib
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_box(nx: int, ny: int, nz: int) -> lbm_box:
+    return lbm_box(int(nx), int(ny), int(nz))
+
+
+def make_eos(kind: str | int = "one_minus_exp", a=1.0, b=4.0, Rgas=1.0, T=0.0) -> lbm_eos:
+    k = PSI_KINDS[kind] if isinstance(kind, str) else int(kind)
+    return lbm_eos(k, float(a), float(b), float(Rgas), float(T))
+
+
+# ---------------------------------------------------------------- same-name wrappers
+
+def lbm_workspace_bytes(box: lbm_box, stencil: int, prec: int) -> int:
+    return int(_lib_.lbm_workspace_bytes(box, int(stencil), int(prec)))
+
+
+def lbm_create(box, tau, G, eos, stencil, prec, dev_workspace: int, nbytes: int, stream: int):
+    out = C.c_void_p()
+    st = _lib_.lbm_create(box, float(tau), float(G), eos, int(stencil), int(prec),
+                          C.c_void_p(dev_workspace), C.c_size_t(nbytes), C.c_void_p(stream),
+                          C.byref(out))
+    check(st, None)
+    return out
+
+
+def lbm_destroy(ctx) -> None:
+    _lib_.lbm_destroy(ctx)
+
+
+def lbm_init_drop(ctx, center, R, rho_in, rho_out, width=1.0):
+    c = np.ascontiguousarray(center, dtype=np.float64)
+    check(_lib_.lbm_init_drop(ctx, _dptr(c), float(R), float(rho_in), float(rho_out), float(width)), ctx)
+
+
+def lbm_init_rho(ctx, host_rho: np.ndarray):
+    r = np.ascontiguousarray(host_rho, dtype=np.float64)
+    check(_lib_.lbm_init_rho(ctx, _dptr(r)), ctx)
+
+
+def lbm_set_populations(ctx, host_f: np.ndarray):
+    f = np.ascontiguousarray(host_f, dtype=np.float64)
+    check(_lib_.lbm_set_populations(ctx, _dptr(f)), ctx)
+
+
+def lbm_get_populations(ctx, out: np.ndarray):
+    check(_lib_.lbm_get_populations(ctx, _dptr(out)), ctx)
+    return out
+
+
+def lbm_step(ctx, n: int):
+    check(_lib_.lbm_step(ctx, int(n)), ctx)
+
+
+def lbm_run_to_convergence(ctx, max_steps=50_000, check_every=2048, tol_dP_rel=1e-5, tol_du=1e-12):
+    """Returns (status, steps_done, criterion); LBM_ENOTCONV is returned, not raised."""
+    steps = C.c_longlong(0)
+    crit = C.c_int(0)
+    st = _lib_.lbm_run_to_convergence(ctx, int(max_steps), int(check_every), float(tol_dP_rel),
+                                      float(tol_du), C.byref(steps), C.byref(crit))
+    if st not in (_lib.LBM_OK, _lib.LBM_ENOTCONV):
+        check(st, ctx)
+    return st, steps.value, crit.value
+
+
+def lbm_observables(ctx) -> lbm_obs:
+    o = lbm_obs()
+    check(_lib_.lbm_observables(ctx, C.byref(o)), ctx)
+    return o
+
+
+def lbm_rho_profile(ctx, length: int) -> np.ndarray:
+    out = np.empty(length)
+    check(_lib_.lbm_rho_profile(ctx, _dptr(out), length), ctx)
+    return out
+
+
+def lbm_pt_profile(ctx, length: int) -> np.ndarray:
+    out = np.empty(length)
+    check(_lib_.lbm_pt_profile(ctx, _dptr(out), length), ctx)
+    return out
+
+
+def lbm_sigma_of_R(ctx, R) -> tuple[np.ndarray, np.ndarray]:
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    s = np.empty_like(R)
+    ds = np.empty_like(R)
+    check(_lib_.lbm_sigma_of_R(ctx, _dptr(R), _dptr(s), _dptr(ds), R.size), ctx)
+    return s, ds
+
+
+def lbm_copy_rho(ctx, out: np.ndarray) -> np.ndarray:
+    check(_lib_.lbm_copy_rho(ctx, _dptr(out)), ctx)
+    return out
+
+
+def lbm_copy_velocity(ctx, out: np.ndarray) -> np.ndarray:
+    check(_lib_.lbm_copy_velocity(ctx, _dptr(out)), ctx)
+    return out
+
+
+def lbm_save(ctx, path: str):
+    check(_lib_.lbm_save(ctx, str(path).encode()), ctx)
+
+
+def lbm_load(ctx, path: str):
+    check(_lib_.lbm_load(ctx, str(path).encode()), ctx)
+
+
+def lbm_autotune(ctx, reps: int = 8) -> int:
+    ch = C.c_longlong(0)
+    check(_lib_.lbm_autotune(ctx, int(reps), C.byref(ch)), ctx)
+    return ch.value
+
+
+def lbm_storage_params(ctx) -> tuple[float, float]:
+    n0 = C.c_double()
+    sc = C.c_double()
+    check(_lib_.lbm_storage_params(ctx, C.byref(n0), C.byref(sc)), ctx)
+    return n0.value, sc.value
+
+
+def lbm_tolman_fit(R_s, sigma_s, is_bubble, quadratic=True) -> tuple[float, float, float]:
+    R = np.ascontiguousarray(R_s, dtype=np.float64)
+    s = np.ascontiguousarray(sigma_s, dtype=np.float64)
+    b = np.ascontiguousarray(is_bubble, dtype=np.int32)
+    s0, d, c = C.c_double(), C.c_double(), C.c_double()
+    check(_lib_.lbm_tolman_fit(_dptr(R), _dptr(s), b.ctypes.data_as(C.POINTER(C.c_int)), R.size,
+                               int(bool(quadratic)), C.byref(s0), C.byref(d), C.byref(c)), None)
+    return s0.value, d.value, c.value
+
+
+# ---------------------------------------------------------------- convenience object
+
+@dataclass
+class Lattice:
+    """One lattice: a torch-owned device workspace plus an lbm_ctx on a stream."""
+    nx: int
+    ny: int
+    nz: int
+    tau: float = 1.0
+    G: float = -5.0
+    psi: str = "one_minus_exp"
+    stencil: str = "E4"
+    prec: str = "f64"
+    cs_T: float = 0.0
+    stream: object = None   # torch.cuda.Stream or None (current stream)
+
+    def __post_init__(self):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Lattice needs a CUDA device (the library has no CPU path)")
+        self.box = make_box(self.nx, self.ny, self.nz)
+        self.eos = make_eos(self.psi, T=self.cs_T)
+        st, pr = STENCILS[self.stencil], PRECS[self.prec]
+        self.nbytes = lbm_workspace_bytes(self.box, st, pr)
+        if self.nbytes == 0:
+            raise LBMError(_lib.LBM_EINVAL, "invalid box/stencil/precision")
+        self.workspace = torch.empty(self.nbytes + 256, dtype=torch.uint8, device="cuda")
+        ptr = self.workspace.data_ptr()
+        ptr += (-ptr) % 256
+        s = self.stream if self.stream is not None else torch.cuda.current_stream()
+        self.stream_handle = s.cuda_stream
+        self.ctx = lbm_create(self.box, self.tau, self.G, self.eos, st, pr, ptr, self.nbytes,
+                              self.stream_handle)
+        self.N = self.nx * self.ny * self.nz
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # thin forwards
+    def init_drop(self, center, R, rho_in, rho_out, width=1.0):
+        lbm_init_drop(self.ctx, center, R, rho_in, rho_out, width)
+
+    def init_rho(self, rho):
+        lbm_init_rho(self.ctx, np.asarray(rho, dtype=np.float64).reshape(-1))
+
+    def set_populations(self, f):
+        lbm_set_populations(self.ctx, np.asarray(f, dtype=np.float64).reshape(-1))
+
+    def get_populations(self) -> np.ndarray:
+        out = np.empty((19, self.nz, self.ny, self.nx))
+        return lbm_get_populations(self.ctx, out)
+
+    def step(self, n: int):
+        lbm_step(self.ctx, n)
+
+    def run_to_convergence(self, **kw):
+        return lbm_run_to_convergence(self.ctx, **kw)
+
+    def observables(self) -> lbm_obs:
+        return lbm_observables(self.ctx)
+
+    def rho(self) -> np.ndarray:
+        out = np.empty((self.nz, self.ny, self.nx))
+        return lbm_copy_rho(self.ctx, out)
+
+    def velocity(self) -> np.ndarray:
+        out = np.empty((3, self.nz, self.ny, self.nx))
+        return lbm_copy_velocity(self.ctx, out)
+
+    def rho_profile(self) -> np.ndarray:
+        return lbm_rho_profile(self.ctx, self.nx // 2 + 1)
+
+    def pt_profile(self) -> np.ndarray:
+        return lbm_pt_profile(self.ctx, self.nx // 2 + 1)
+
+    def sigma_of_R(self, R):
+        return lbm_sigma_of_R(self.ctx, R)
+
+    def autotune(self, reps=8) -> int:
+        return lbm_autotune(self.ctx, reps)
+
+    def storage_params(self):
+        return lbm_storage_params(self.ctx)
+
+    def save(self, path):
+        lbm_save(self.ctx, path)
+
+    def load(self, path):
+        lbm_load(self.ctx, path)

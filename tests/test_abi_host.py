@@ -1,0 +1,123 @@
+"""Host-side checks of the C ABI: the library loads, exports every declared symbol, and
+rejects bad arguments before touching a GPU."""
+import ctypes as C
+import re
+import subprocess
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import paper_2105_08772_gb300 as P
+from paper_2105_08772_gb300 import _lib
+from oracle import observables as O
+
+ROOT = Path(__file__).resolve().parent.parent
+HEADER = ROOT / "include" / "lbm.h"
+
+
+def declared_functions():
+    text = HEADER.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-zA-Z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_what_the_binding_knows():
+    assert declared_functions() == sorted(_lib.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    for name in declared_functions():
+        assert hasattr(_lib.lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", str(_lib._LIB_PATH)], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (lbm_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """ctypes mirrors of the header structs have the C compiler's sizes and offsets."""
+    fields = [f for f, _ in _lib.lbm_obs._fields_]
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "lbm.h"', "int main(void) {",
+           'printf("%zu %zu %zu\\n", sizeof(lbm_box), sizeof(lbm_eos), sizeof(lbm_obs));']
+    src += [f'printf("%zu\\n", offsetof(lbm_obs, {f}));' for f in fields]
+    src += ["return 0; }"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", str(ROOT / "include"), str(c), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert [int(v) for v in out[:3]] == [C.sizeof(_lib.lbm_box), C.sizeof(_lib.lbm_eos),
+                                         C.sizeof(_lib.lbm_obs)]
+    assert [int(v) for v in out[3:]] == [getattr(_lib.lbm_obs, f).offset for f in fields]
+
+
+def test_workspace_bytes():
+    b = P.make_box(128, 128, 128)
+    n = 128 ** 3
+    got = P.lbm_workspace_bytes(b, 4, 1)
+    assert got >= 2 * 19 * n * 4 + 3 * n * 4
+    assert P.lbm_workspace_bytes(b, 4, 0) >= 2 * 19 * n * 8
+    assert P.lbm_workspace_bytes(P.make_box(2, 8, 8), 4, 0) == 0     # too small for E4
+    assert P.lbm_workspace_bytes(P.make_box(4, 8, 8), 6, 0) == 0     # too small for E6
+    assert P.lbm_workspace_bytes(b, 5, 0) == 0                       # no such stencil
+    assert P.lbm_workspace_bytes(b, 4, 7) == 0                       # no such precision
+
+
+def _create(**kw):
+    args = dict(box=P.make_box(16, 16, 16), tau=1.0, G=-5.0, eos=P.make_eos("one_minus_exp"),
+                stencil=4, prec=0, ws=256 * 1024, nbytes=1 << 40, stream=0)
+    args.update(kw)
+    out = C.c_void_p()
+    st = _lib.lib.lbm_create(args["box"], args["tau"], args["G"], args["eos"], args["stencil"],
+                             args["prec"], C.c_void_p(args["ws"]), C.c_size_t(args["nbytes"]),
+                             C.c_void_p(args["stream"]), C.byref(out))
+    return st, _lib.lib.lbm_last_error(None).decode(), out
+
+
+@pytest.mark.parametrize("kw,status,msg", [
+    (dict(G=-3.9), _lib.LBM_EINVAL, "G_c = -4"),
+    (dict(G=-7.0, eos=P.make_eos("exp_inv")), _lib.LBM_EINVAL, "exp(-1/n)"),
+    (dict(tau=0.5), _lib.LBM_EINVAL, "tau"),
+    (dict(box=P.make_box(2, 16, 16)), _lib.LBM_EINVAL, "too small"),
+    (dict(box=P.make_box(4, 16, 16), stencil=8), _lib.LBM_EINVAL, "too small"),
+    (dict(stencil=5), _lib.LBM_EINVAL, "stencil"),
+    (dict(prec=3), _lib.LBM_EINVAL, "prec"),
+    (dict(ws=0), _lib.LBM_EINVAL, "null"),
+    (dict(ws=256 * 1024 + 8), _lib.LBM_EINVAL, "aligned"),
+    (dict(nbytes=1000), _lib.LBM_ENOMEM, "needs"),
+    (dict(eos=P.make_eos("cs", T=0.0), G=-1.0), _lib.LBM_EINVAL, "Carnahan"),
+    (dict(eos=P.make_eos(9)), _lib.LBM_EINVAL, "kind"),
+])
+def test_create_rejects_bad_arguments_before_any_gpu_work(kw, status, msg):
+    st, err, out = _create(**kw)
+    assert st == status and msg in err and not out.value
+
+
+def test_null_context_calls_fail_cleanly():
+    assert _lib.lib.lbm_step(None, 1) == _lib.LBM_EINVAL
+    assert _lib.lib.lbm_observables(None, None) == _lib.LBM_EINVAL
+    _lib.lib.lbm_destroy(None)
+    assert _lib.lib.lbm_strerror(_lib.LBM_ENOTCONV) == b"not converged"
+
+
+def test_tolman_fit_matches_oracle():
+    rng = np.random.default_rng(5)
+    Rs = rng.uniform(5, 40, size=30)
+    bub = (rng.uniform(size=30) < 0.5).astype(np.int32)
+    x = np.where(bub == 1, -1.0, 1.0) / Rs
+    sig = 0.036 * (1 - 2 * 1.3 * x + 2.0 * x * x) + 1e-6 * rng.normal(size=30)
+    for quad in (True, False):
+        got = P.lbm_tolman_fit(Rs, sig, bub, quadratic=quad)
+        ref = O.tolman_fit(Rs, sig, bub, quadratic=quad)
+        assert np.allclose(got, ref, rtol=1e-9, atol=1e-12)
+
+
+def test_tolman_fit_skips_points_without_a_minimum():
+    Rs = np.array([6.0, np.nan, 10.0, 14.0, 20.0])
+    sig = np.array([0.03, np.nan, 0.032, 0.033, 0.034])
+    s0, d, c = P.lbm_tolman_fit(Rs, sig, np.zeros(5, dtype=np.int32), quadratic=False)
+    s0r, dr, _ = O.tolman_fit(Rs[np.isfinite(Rs)], sig[np.isfinite(sig)], np.zeros(4), quadratic=False)
+    assert abs(s0 - s0r) < 1e-14 and abs(d - dr) < 1e-12
+    with pytest.raises(P.LBMError):
+        P.lbm_tolman_fit(Rs[:1], sig[:1], np.zeros(1, dtype=np.int32), quadratic=False)

@@ -1,0 +1,257 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: density max-abs 1e-11 on the FP64 path and 1e-4 relative on the
+FP32-shifted path after 1000 steps.  FP16-shifted storage is checked against a
+bound derived from half precision (11-bit significand) and reported.
+"""
+import numpy as np
+import pytest
+
+import inputs
+import paper_2105_08772_gb300 as P
+from oracle import eos as E
+from oracle import lbm3d
+from oracle import observables as O
+
+pytestmark = pytest.mark.gpu
+
+G = -5.0
+
+
+def oracle_model(G=G, kind="one_minus_exp", stencil="E4", tau=1.0, T=0.0):
+    return lbm3d.Model(tau=tau, G=G, eos=E.EOS(kind, T=T), stencil=stencil)
+
+
+def lattice(shape_zyx, prec="f64", stencil="E4", kind="one_minus_exp", G=G, tau=1.0, T=0.0):
+    nz, ny, nx = shape_zyx
+    return P.Lattice(nx, ny, nz, tau=tau, G=G, psi=kind, stencil=stencil, prec=prec, cs_T=T)
+
+
+SHAPE = (12, 20, 40)          # z, y, x: 2 x-tiles (one ragged), ragged y tiles, one z chunk
+RAGGED = (23, 29, 37)
+
+
+@pytest.fixture(scope="module")
+def random_state():
+    f0 = inputs.random_populations(SHAPE, seed=11)
+    ref = lbm3d.run(f0, oracle_model(), 1000)
+    return f0, ref
+
+
+def test_population_roundtrip_is_exact():
+    f0 = inputs.random_populations((7, 9, 11), seed=1)
+    lat = lattice((7, 9, 11))
+    lat.set_populations(f0)
+    assert np.array_equal(lat.get_populations(), f0)
+
+
+def test_single_step_matches_oracle_f64():
+    f0 = inputs.random_populations(RAGGED, seed=2)
+    lat = lattice(RAGGED)
+    lat.set_populations(f0)
+    lat.step(1)
+    ref = lbm3d.step(f0, oracle_model())
+    assert np.max(np.abs(lat.get_populations() - ref)) < 1e-14
+
+
+def test_parity_f64_1000_steps(random_state):
+    f0, ref = random_state
+    lat = lattice(SHAPE)
+    lat.set_populations(f0)
+    lat.step(1000)
+    rho, rho_ref = lat.rho(), lbm3d.density(ref)
+    assert np.max(np.abs(rho - rho_ref)) < 1e-11
+    assert np.max(np.abs(lat.get_populations() - ref)) < 1e-11
+
+
+def test_parity_f32_shifted_1000_steps(random_state):
+    f0, ref = random_state
+    lat = lattice(SHAPE, prec="f32")
+    lat.set_populations(f0)
+    lat.step(1000)
+    rho_ref = lbm3d.density(ref)
+    rel = np.max(np.abs(lat.rho() - rho_ref) / rho_ref)
+    assert rel < 1e-4, rel
+
+
+def test_parity_f16_shifted_1000_steps(random_state):
+    """Half storage rounds each shifted population to 2^-11 relative every step; the bound
+    below is that rounding times the population scale, accumulated over the run."""
+    f0, ref = random_state
+    lat = lattice(SHAPE, prec="f16")
+    lat.set_populations(f0)
+    lat.step(1000)
+    rho_ref = lbm3d.density(ref)
+    rel = np.max(np.abs(lat.rho() - rho_ref) / rho_ref)
+    print(f"f16 shifted: max relative density error after 1000 steps {rel:.3e}")
+    assert np.isfinite(rel) and rel < 5e-2
+
+
+def test_droplet_init_matches_oracle():
+    shape = (16, 24, 32)
+    lat = lattice(shape)
+    c = (16, 12, 8)
+    lat.init_drop(c, 6.0, 1.89, 0.12, 1.0)
+    f = lbm3d.init_from_density(lbm3d.drop_density(shape, c, 6.0, 1.89, 0.12))
+    assert np.max(np.abs(lat.get_populations() - f)) < 1e-14
+    lat.step(300)
+    ref = lbm3d.run(f, oracle_model(), 300)
+    assert np.max(np.abs(lat.rho() - lbm3d.density(ref))) < 1e-11
+
+
+def test_init_rho_matches_init_from_density():
+    shape = (10, 12, 14)
+    n = inputs.random_density(shape, seed=3)
+    lat = lattice(shape)
+    lat.init_rho(n)
+    assert np.max(np.abs(lat.get_populations() - lbm3d.init_from_density(n))) < 1e-15
+
+
+@pytest.mark.parametrize("stencil", ["E6", "E8"])
+def test_parity_wide_stencils_f64(stencil):
+    shape = (10, 14, 20)
+    f0 = inputs.random_populations(shape, seed=4)
+    lat = lattice(shape, stencil=stencil)
+    lat.set_populations(f0)
+    lat.step(200)
+    ref = lbm3d.run(f0, oracle_model(stencil=stencil), 200)
+    assert np.max(np.abs(lat.get_populations() - ref)) < 1e-11
+
+
+@pytest.mark.parametrize("kind,Gk,T", [("exp_inv", -9.2, 0.0), ("cs", -1.0, 0.085)])
+def test_parity_other_pseudopotentials_f64(kind, Gk, T):
+    shape = (10, 12, 18)
+    if kind == "cs":
+        f0 = inputs.random_populations(shape, seed=5, inner=0.3, outer=0.05)
+    else:
+        f0 = inputs.random_populations(shape, seed=5, inner=2.3, outer=0.45)
+    lat = lattice(shape, kind=kind, G=Gk, T=T)
+    lat.set_populations(f0)
+    lat.step(200)
+    ref = lbm3d.run(f0, oracle_model(G=Gk, kind=kind, T=T), 200)
+    assert np.max(np.abs(lat.get_populations() - ref)) < 1e-11
+
+
+@pytest.mark.parametrize("shape,stencil", [((3, 3, 3), "E4"), ((5, 5, 5), "E6"), ((4, 3, 7), "E4"),
+                                           ((5, 6, 5), "E8")])
+def test_minimum_boxes(shape, stencil):
+    f0 = inputs.random_populations(shape, seed=6)
+    lat = lattice(shape, stencil=stencil)
+    lat.set_populations(f0)
+    lat.step(50)
+    ref = lbm3d.run(f0, oracle_model(stencil=stencil), 50)
+    assert np.max(np.abs(lat.get_populations() - ref)) < 1e-12
+
+
+def test_tau_other_than_one():
+    f0 = inputs.random_populations((8, 10, 12), seed=7)
+    lat = lattice((8, 10, 12), tau=0.7)
+    lat.set_populations(f0)
+    lat.step(100)
+    ref = lbm3d.run(f0, oracle_model(tau=0.7), 100)
+    assert np.max(np.abs(lat.get_populations() - ref)) < 1e-11
+
+
+def test_graph_replay_equals_eager_steps():
+    f0 = inputs.random_populations((12, 16, 20), seed=8)
+    a = lattice((12, 16, 20))
+    a.set_populations(f0)
+    a.step(300)                 # graph replays + eager remainder
+    b = lattice((12, 16, 20))
+    b.set_populations(f0)
+    for _ in range(300):
+        b.step(1)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+
+
+def test_every_tile_shape_gives_identical_results():
+    """The per-node arithmetic does not depend on the tiling: bitwise-equal fields."""
+    f0 = inputs.random_populations(RAGGED, seed=9)
+    lat = lattice(RAGGED)
+    lat.set_populations(f0)
+    choice = lat.autotune(reps=2)
+    assert choice > 0
+    steps_done = lat.observables().steps
+    ref = lbm3d.run(f0, oracle_model(), steps_done)
+    assert np.max(np.abs(lat.get_populations() - ref)) < 1e-12
+
+
+def test_observables_match_oracle():
+    shape = (24, 26, 28)
+    f0 = inputs.random_populations(shape, seed=10, inner=1.85, outer=0.13, noise=0.0)
+    lat = lattice(shape)
+    lat.set_populations(f0)
+    lat.step(200)
+    ob = lat.observables()
+    fr = lbm3d.run(f0, oracle_model(), 200)
+    ref = O.observe(fr, oracle_model(), contrast0=None)
+    for k in ("n_in", "n_out", "P_in", "P_out", "dP", "mass", "R_e", "C", "D", "max_u"):
+        a, b = getattr(ob, k), getattr(ref, k)
+        assert abs(a - b) <= 1e-10 * max(1.0, abs(b)), (k, a, b)
+    assert np.allclose(list(ob.com), ref.com, atol=1e-9)
+    if np.isfinite(ref.R_s):
+        assert abs(ob.R_s - ref.R_s) < 1e-9 * ref.R_s
+    else:
+        assert np.isnan(ob.R_s) and (ob.status_bits & 1)
+    assert np.max(np.abs(lat.pt_profile() - ref.PT_line)) < 1e-12
+    assert np.max(np.abs(lat.rho_profile() - ref.n_line)) < 1e-12
+    u = lat.velocity()
+    assert np.max(np.abs(u - O.velocity(fr, oracle_model()))) < 1e-12
+
+
+def test_delta_u_matches_oracle():
+    shape = (10, 12, 14)
+    f0 = inputs.random_populations(shape, seed=12)
+    lat = lattice(shape)
+    lat.set_populations(f0)
+    lat.observables()                 # snapshot u(t)
+    lat.step(40)
+    ob = lat.observables()
+    m = oracle_model()
+    u0 = O.velocity(f0, m)
+    u1 = O.velocity(lbm3d.run(f0, m, 40), m)
+    assert abs(ob.du - O.delta_u(u1, u0)) < 1e-12
+
+
+def test_sigma_of_R_uses_the_measured_integrals():
+    shape = (24, 26, 28)
+    f0 = inputs.random_populations(shape, seed=10, inner=1.85, outer=0.13, noise=0.0)
+    lat = lattice(shape)
+    lat.set_populations(f0)
+    ob = lat.observables()
+    R = np.array([2.0, 5.0, 9.5])
+    s, ds = lat.sigma_of_R(R)
+    s_ref, ds_ref = O.sigma_of_R(R, ob.dP, ob.C, ob.D)
+    assert np.allclose(s, s_ref, rtol=1e-14) and np.allclose(ds, ds_ref, rtol=1e-14)
+
+
+def test_save_load_resumes_bitwise(tmp_path):
+    f0 = inputs.random_populations((8, 9, 10), seed=13)
+    a = lattice((8, 9, 10), prec="f32")
+    a.set_populations(f0)
+    a.step(50)
+    a.save(tmp_path / "ck.bin")
+    a.step(77)
+    b = lattice((8, 9, 10), prec="f32")
+    b.load(tmp_path / "ck.bin")
+    b.step(77)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    assert b.observables().steps == 127
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_full_size_steps_in_bench_configuration(prec):
+    """128^3 (the benchmark box) in the benchmark's tiling: two steps (both buffer parities)
+    against the oracle on the whole field."""
+    shape = (128, 128, 128)
+    f0 = inputs.random_populations(shape, seed=14, inner=1.89, outer=0.15, radius=32.0)
+    lat = lattice(shape, prec=prec)
+    lat.set_populations(f0)
+    m = oracle_model()
+    ref = f0
+    for k in range(2):
+        lat.step(1)
+        ref = lbm3d.step(ref, m)
+        rho_ref = lbm3d.density(ref)
+        err = np.max(np.abs(lat.rho() - rho_ref) / rho_ref)
+        assert err < (1e-14 if prec == "f64" else 2e-6), (k, err)

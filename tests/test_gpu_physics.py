@@ -1,0 +1,113 @@
+"""Properties of converged GPU runs that hold at any size (Secs. II-IV).
+
+These runs are too long for the oracle, so they are checked against what the
+paper and the mathematics fix: conservation, symmetry, the convergence tests,
+mechanical equilibrium, the generalised Laplace law and Laplace's law at
+large R against the oracle's flat-interface sigma_0.
+"""
+import numpy as np
+import pytest
+
+import paper_2105_08772_gb300 as P
+from oracle import eos as E
+from oracle import flat
+
+pytestmark = pytest.mark.gpu
+
+G = -5.0
+
+
+@pytest.fixture(scope="module")
+def coexist():
+    r = flat.run_flat(G, E.EOS("one_minus_exp"), Lx=100)
+    return r
+
+
+def test_mass_conserved_over_a_long_fp64_run(coexist):
+    lat = P.Lattice(64, 64, 64, G=G, prec="f64")
+    lat.init_drop((32, 32, 32), 16.0, coexist.n_l, coexist.n_g)
+    m0 = lat.observables().mass
+    lat.step(4096)
+    m1 = lat.observables().mass
+    assert abs(m1 - m0) / m0 < 1e-13
+
+
+def test_fp32_shifted_mass_drift_small(coexist):
+    lat = P.Lattice(64, 64, 64, G=G, prec="f32")
+    lat.init_drop((32, 32, 32), 16.0, coexist.n_l, coexist.n_g)
+    m0 = lat.observables().mass
+    lat.step(4096)
+    assert abs(lat.observables().mass - m0) / m0 < 1e-5
+
+
+@pytest.fixture(scope="module")
+def converged_128(coexist):
+    out = {}
+    for kind in ("droplet", "bubble"):
+        lat = P.Lattice(128, 128, 128, G=G, prec="f64")
+        n_in, n_out = (coexist.n_l, coexist.n_g) if kind == "droplet" else (coexist.n_g, coexist.n_l)
+        lat.init_drop((64, 64, 64), 32.0, n_in, n_out)
+        st, steps, crit = lat.run_to_convergence(max_steps=50_000, check_every=2048)
+        out[kind] = (lat, st, steps, crit, lat.observables())
+    return out
+
+
+@pytest.mark.parametrize("kind", ["droplet", "bubble"])
+def test_128_converges_by_a_paper_criterion(converged_128, kind):
+    lat, st, steps, crit, ob = converged_128[kind]
+    assert st == 0 and crit in (1, 2), (st, steps, crit)
+    assert not (ob.status_bits & 2)              # not collapsed
+    assert not (ob.status_bits & 4)              # centre of mass within 1e-3 (Sec. IV)
+    assert not (ob.status_bits & 8)
+    assert ob.dP > 0                             # Laplace: inside pressure higher
+
+
+@pytest.mark.parametrize("kind", ["droplet", "bubble"])
+def test_128_mechanical_equilibrium_moment(converged_128, kind):
+    """n = d - 1 identity of Eq. (17): int 2 r (P_T - P_out) dr vanishes at equilibrium."""
+    lat, st, steps, crit, ob = converged_128[kind]
+    PT = lat.pt_profile()
+    r = np.arange(len(PT))
+    scale = np.trapezoid(2 * r * np.abs(PT - ob.P_out), r)
+    assert abs(2 * ob.D) < 0.02 * scale
+
+
+@pytest.mark.parametrize("kind", ["droplet", "bubble"])
+def test_128_surface_of_tension(converged_128, kind):
+    lat, st, steps, crit, ob = converged_128[kind]
+    if ob.status_bits & 1:
+        pytest.skip("sigma[R] has no minimum for this field")
+    R = np.linspace(0.5, 2.0, 31) * ob.R_s
+    s, ds = lat.sigma_of_R(R)
+    s_s = 0.5 * ob.dP * ob.R_s
+    assert abs(ob.sigma_s - s_s) < 1e-14
+    assert s.min() >= s_s * (1 - 1e-12)
+    # universal curve (Sec. III below Eq. (22))
+    assert np.max(np.abs(s / s_s - ((ob.R_s / R) ** 2 / 3 + 2 * R / (3 * ob.R_s)))) < 1e-10
+    # generalised Laplace law Eq. (11) with Eq. (22): residual is the equilibrium moment 2D/R^2
+    assert np.max(np.abs(2 * s / R + ds - ob.dP - 2 * ob.D / R ** 2)) < 1e-12
+
+
+def test_128_droplet_symmetric(converged_128):
+    lat = converged_128["droplet"][0]
+    rho = lat.rho()
+    for perm in ((0, 2, 1), (1, 0, 2), (2, 1, 0)):
+        assert np.max(np.abs(rho - rho.transpose(perm))) < 1e-10
+    # reflection about the centre node 64 (minimum image)
+    ref = np.roll(np.flip(rho, axis=2), 1, axis=2)
+    assert np.max(np.abs(rho - ref)) < 1e-10
+
+
+def test_fp32_shifted_reproduces_fp64_observables(coexist, converged_128):
+    """Mixed precision (FP32 storage/collision, FP64 reductions) against the FP64 GPU run."""
+    lat64, _, _, _, ob64 = converged_128["droplet"]
+    lat = P.Lattice(128, 128, 128, G=G, prec="f32")
+    lat.init_drop((64, 64, 64), 32.0, coexist.n_l, coexist.n_g)
+    st, steps, crit = lat.run_to_convergence(max_steps=50_000, check_every=2048)
+    ob = lat.observables()
+    assert crit in (1, 2)
+    for k in ("n_in", "n_out", "dP", "R_e"):
+        a, b = getattr(ob, k), getattr(ob64, k)
+        assert abs(a - b) / abs(b) < 1e-3, (k, a, b)
+    if np.isfinite(ob64.R_s):
+        assert abs(ob.R_s - ob64.R_s) / ob64.R_s < 1e-3
