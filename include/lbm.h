@@ -137,7 +137,8 @@ void lbm_destroy(lbm_ctx* ctx);
  * Eq. (23): n(r) = (rho_in + rho_out)/2 - (rho_in - rho_out)/2 tanh((r - R)/width),
  * r the minimum-image distance to center[3] = (x, y, z) (host array of 3), fluid at
  * rest: f_i = f_i^eq(n, u = 0) (Eq. (6)).  width = 1 is the paper's profile.
- * Resets the step counter and the convergence history.  Async. */
+ * For shifted storage the shift n0 is the mean density of a sharp sphere of
+ * radius R.  Resets the step counter and the convergence history.  Async. */
 lbm_status lbm_init_drop(lbm_ctx* ctx, const double center[3], double R,
                          double rho_in, double rho_out, double width);
 
@@ -201,11 +202,20 @@ lbm_status lbm_copy_velocity(lbm_ctx* ctx, double* host_out);
 lbm_status lbm_save(lbm_ctx* ctx, const char* path);
 lbm_status lbm_load(lbm_ctx* ctx, const char* path);
 
-/* Choose the step kernel's tile shape and z-chunk for this context by timing
- * candidates on the current field (which it advances by an even number of steps
- * and then restores).  Optional; lbm_create starts from a size-based default.
- * Synchronises.  *choice (may be null) receives bx*1000000 + by*10000 + zchunk. */
+/* Choose the step kernel's configuration for this context by timing every
+ * compiled candidate for reps (rounded up to even) steps on the current field.
+ * The field advances by those steps (the step counter counts them).  Optional;
+ * lbm_create starts from a size-based default.  Synchronises.  *choice (may be
+ * null) receives the chosen code (see lbm_set_tile). */
 lbm_status lbm_autotune(lbm_ctx* ctx, int reps, long long* choice);
+
+/* Select the step kernel's configuration by the code lbm_autotune reports:
+ * kind * 10^8 + bx * 10^6 + by * 10^4 + (kind ? prefetch depth : z chunk), kind 0 the
+ * register-load kernel, 1 the cp.async-pipelined kernel (F32/F64 storage only).  A code
+ * that is not compiled for this context's precision and stencil gives LBM_EINVAL.
+ * lbm_get_tile returns the current code.  Results do not depend on the choice. */
+lbm_status lbm_set_tile(lbm_ctx* ctx, long long code);
+lbm_status lbm_get_tile(const lbm_ctx* ctx, long long* code);
 
 /* Shift n0 and storage scale of the populations (F32/F16 modes; 0 and 1 for F64). */
 lbm_status lbm_storage_params(const lbm_ctx* ctx, double* n0, double* scale);

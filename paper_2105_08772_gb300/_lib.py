@@ -27,7 +27,8 @@ EXPORTS = (
     "lbm_workspace_bytes", "lbm_create", "lbm_destroy", "lbm_init_drop", "lbm_init_rho",
     "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_run_to_convergence",
     "lbm_observables", "lbm_rho_profile", "lbm_pt_profile", "lbm_sigma_of_R", "lbm_copy_rho",
-    "lbm_copy_velocity", "lbm_save", "lbm_load", "lbm_autotune", "lbm_storage_params",
+    "lbm_copy_velocity", "lbm_save", "lbm_load", "lbm_autotune", "lbm_set_tile", "lbm_get_tile",
+    "lbm_storage_params",
     "lbm_strerror", "lbm_last_error", "lbm_tolman_fit",
 )
 
@@ -64,7 +65,7 @@ _D = C.POINTER(C.c_double)
 def _load():
     if not _LIB_PATH.exists():
         raise ImportError(f"{_LIB_PATH} is missing: build it with "
-                          "`python -m paper_2105_08772_gb300.build` (there is no CPU fallback)")
+                          "`python paper_2105_08772_gb300/build.py` (there is no CPU fallback)")
     lib = C.CDLL(str(_LIB_PATH))
     sig = {
         "lbm_workspace_bytes": (C.c_size_t, [lbm_box, C.c_int, C.c_int]),
@@ -87,6 +88,8 @@ def _load():
         "lbm_save": (C.c_int, [_P, C.c_char_p]),
         "lbm_load": (C.c_int, [_P, C.c_char_p]),
         "lbm_autotune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong)]),
+        "lbm_set_tile": (C.c_int, [_P, C.c_longlong]),
+        "lbm_get_tile": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
         "lbm_storage_params": (C.c_int, [_P, _D, _D]),
         "lbm_strerror": (C.c_char_p, [C.c_int]),
         "lbm_last_error": (C.c_char_p, [_P]),

@@ -2,7 +2,8 @@
 
 Each CUDA translation unit is compiled to an object in parallel, then linked
 into ``paper_2105_08772_gb300/liblbm.so``.  Objects go to ``_build/`` next to
-this file.  Usage:  python -m paper_2105_08772_gb300.build [--force]
+this file.  Usage:  python paper_2105_08772_gb300/build.py [--force] [--ptxas-v]
+(run as a script: the package refuses to import until the library exists).
 """
 from __future__ import annotations
 

@@ -82,6 +82,7 @@ bool valid_stencil(int s) { return s == 4 || s == 6 || s == 8; }
 bool valid_prec(int p) { return p == kF64 || p == kF32 || p == kF16; }
 
 constexpr int kObsBX = 32, kObsBY = 4;
+constexpr size_t kMaxSmemPerCta = 227 * 1024;   // opt-in limit of one CTA on sm_103
 
 int default_obs_zchunk(lbm_box b) { return b.nz < 8 ? b.nz : 8; }
 
@@ -89,6 +90,10 @@ long long obs_partials(lbm_box b, int zchunk) {
   return (long long)((b.nx + kObsBX - 1) / kObsBX) * ((b.ny + kObsBY - 1) / kObsBY) *
          ((b.nz + zchunk - 1) / zchunk);
 }
+
+constexpr size_t kStateDP = 64;     // offsets inside the state block
+constexpr size_t kStateObs = 128;
+static_assert(sizeof(PointOut) <= kStateDP, "PointOut overlaps dP_prev");
 
 struct Layout {
   size_t pop, u_old, partials, state, lines, total;
@@ -102,7 +107,8 @@ Layout layout_of(lbm_box b, int prec) {
   L.pop = align256((size_t)Q * N * storage_bytes(prec));
   L.u_old = align256(3 * N * (prec == kF64 ? 8 : 4));
   L.partials = align256((size_t)L.npart * sizeof(FieldPartial));
-  L.state = align256(sizeof(PointOut) + sizeof(double) + sizeof(lbm_obs) + 64);
+  // state block: PointOut at 0, dP_prev at kStateDP, the lbm_obs record at kStateObs
+  L.state = align256(kStateObs + sizeof(lbm_obs));
   L.lines = align256(2 * sizeof(double) * (size_t)(b.nx / 2 + 1));
   L.total = 2 * L.pop + L.u_old + L.partials + L.state + L.lines;
   return L;
@@ -137,10 +143,52 @@ LatticeDesc desc_of(const lbm_ctx* c, int src_buf) {
 
 TileCfg default_tile(lbm_box b, int prec, int stencil) {
   TileCfg t;
+  t.zchunk = b.nz < 16 ? b.nz : 16;
+  if (prec == kF16) {   // register-load kernel
+    t.bx = 32;
+    t.by = stencil == 4 ? 8 : 4;
+    return t;
+  }
+  t.kind = 1;           // pipelined kernel
   t.bx = 32;
   t.by = (prec == kF64 || stencil != 4) ? 4 : 8;
-  t.zchunk = b.nz < 16 ? b.nz : 16;
+  t.depth = (stencil == 4 && prec == kF64) ? 2 : 1;
   return t;
+}
+
+long long tile_code(const TileCfg& t) {
+  return (long long)t.kind * 100000000 + (long long)t.bx * 1000000 + t.by * 10000 +
+         (t.kind == 1 ? t.depth : t.zchunk);
+}
+
+// every step configuration compiled for this precision and stencil
+std::vector<TileCfg> step_candidates(const lbm_ctx* c) {
+  std::vector<TileCfg> out;
+  const int (*shapes)[2] = c->stencil == 4 ? kShapesE4 : kShapesWide;
+  const int ns = c->stencil == 4 ? kNumShapesE4 : kNumShapesWide;
+  const int zcands[] = {4, 8, 16, 32, 64};
+  for (int k = 0; k < ns; ++k)
+    for (int zc : zcands) {
+      if (zc > c->box.nz && zc != 4) continue;
+      TileCfg t{shapes[k][0], shapes[k][1], zc < c->box.nz ? zc : c->box.nz};
+      out.push_back(t);
+    }
+  if (c->prec != kF16) {
+    const int (*as)[3] = c->stencil == 4 ? kAsyncE4 : kAsyncWide;
+    const int na = c->stencil == 4 ? kNumAsyncE4 : kNumAsyncWide;
+    const int R = radius_of(c->stencil);
+    for (int k = 0; k < na; ++k) {
+      TileCfg t{as[k][0], as[k][1], 1};
+      t.kind = 1;
+      t.depth = as[k][2];
+      // shared memory of the pipelined kernel: (R + 1 + depth) population stages and
+      // 2R + 1 psi planes of the padded tile; skip what does not fit one CTA
+      const size_t pad = (size_t)(t.bx + 2 * R) * (t.by + 2 * R);
+      const size_t smem = storage_bytes(c->prec) * pad * ((R + 1 + t.depth) * Q + 2 * R + 1);
+      if (smem <= kMaxSmemPerCta) out.push_back(t);
+    }
+  }
+  return out;
 }
 
 void drop_graphs(lbm_ctx* c) {
@@ -155,13 +203,13 @@ lbm_status prepare_kernels(lbm_ctx* c) {
   // outside any stream capture
   LatticeDesc d = desc_of(c, 0);
   ObsArgs oa{};
-  const int (*shapes)[2] = c->stencil == 4 ? kShapesE4 : kShapesWide;
-  const int ns = c->stencil == 4 ? kNumShapesE4 : kNumShapesWide;
-  for (int k = 0; k < ns; ++k) {
-    TileCfg t{shapes[k][0], shapes[k][1], 0};
-    LBM_CUDA(c, launch_lattice(c->prec, c->stencil, kModeStep, d, t, oa, c->stream));
+  for (const TileCfg& t : step_candidates(c)) {
+    TileCfg p = t;
+    p.prepare = true;
+    LBM_CUDA(c, launch_lattice(c->prec, c->stencil, kModeStep, d, p, oa, c->stream));
   }
   TileCfg t{kObsBX, kObsBY, 0};
+  t.prepare = true;
   LBM_CUDA(c, launch_lattice(c->prec, c->stencil, kModeObs, d, t, oa, c->stream));
   return LBM_OK;
 }
@@ -332,8 +380,8 @@ lbm_status lbm_create(lbm_box box, double tau, double G, lbm_eos eos, int stenci
   c->partials = reinterpret_cast<FieldPartial*>(p); p += L.partials;
   c->max_partials = L.npart;
   c->pts = reinterpret_cast<PointOut*>(p);
-  c->dP_prev = reinterpret_cast<double*>(p + 64);
-  c->obs_dev = reinterpret_cast<lbm_obs*>(p + 128);
+  c->dP_prev = reinterpret_cast<double*>(p + kStateDP);
+  c->obs_dev = reinterpret_cast<lbm_obs*>(p + kStateObs);
   p += L.state;
   c->line_len = box.nx / 2 + 1;
   c->n_line = reinterpret_cast<double*>(p);
@@ -377,7 +425,12 @@ lbm_status lbm_init_drop(lbm_ctx* c, const double center[3], double R, double rh
     return fail(c, LBM_EINVAL, "R, width and densities must be positive and finite");
   for (int k = 0; k < 3; ++k)
     if (!isfinite(center[k])) return fail(c, LBM_EINVAL, "center must be finite");
-  choose_storage(c, 0.5 * (rho_in + rho_out), (1.0 / 3.0) * fabs(rho_in - rho_out));
+  // shift: the mean density of a sharp sphere of radius R in the box, so that
+  // the phase filling most of the volume is stored with the smallest values
+  const double V = (double)c->box.nx * c->box.ny * c->box.nz;
+  const double frac = fmin(1.0, 4.0 * M_PI * R * R * R / (3.0 * V));
+  const double mean = rho_out + (rho_in - rho_out) * frac;
+  choose_storage(c, mean, (1.0 / 3.0) * fmax(fabs(rho_in - mean), fabs(rho_out - mean)));
   c->cur = 0;
   drop_graphs(c);
   DropInit di{center[0], center[1], center[2], R, rho_in, rho_out, width};
@@ -653,33 +706,26 @@ lbm_status lbm_autotune(lbm_ctx* c, int reps, long long* choice) {
   LBM_CHECK_INIT(c);
   if (reps < 2) reps = 2;
   reps += reps & 1;
-  const int (*shapes)[2] = c->stencil == 4 ? kShapesE4 : kShapesWide;
-  const int ns = c->stencil == 4 ? kNumShapesE4 : kNumShapesWide;
-  const int zcands[] = {4, 8, 16, 32, 64};
   cudaEvent_t e0, e1;
   LBM_CUDA(c, cudaEventCreate(&e0));
   LBM_CUDA(c, cudaEventCreate(&e1));
   TileCfg best = c->step_cfg;
   float best_ms = 1e30f;
   lbm_status st = LBM_OK;
-  for (int k = 0; k < ns && st == LBM_OK; ++k) {
-    for (int zc : zcands) {
-      if (zc > c->box.nz && zc != 4) continue;
-      TileCfg t{shapes[k][0], shapes[k][1], zc < c->box.nz ? zc : c->box.nz};
-      c->step_cfg = t;
-      st = launch_steps_eager(c, 2, c->stream);
-      if (st != LBM_OK) break;
-      cudaEventRecord(e0, c->stream);
-      st = launch_steps_eager(c, reps, c->stream);
-      if (st != LBM_OK) break;
-      cudaEventRecord(e1, c->stream);
-      cudaError_t e = cudaEventSynchronize(e1);
-      if (e != cudaSuccess) { st = fail(c, LBM_ECUDA, "autotune: %s", cudaGetErrorString(e)); break; }
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      c->steps += reps + 2;
-      if (ms < best_ms) { best_ms = ms; best = t; }
-    }
+  for (const TileCfg& t : step_candidates(c)) {
+    c->step_cfg = t;
+    st = launch_steps_eager(c, 2, c->stream);
+    if (st != LBM_OK) break;
+    cudaEventRecord(e0, c->stream);
+    st = launch_steps_eager(c, reps, c->stream);
+    if (st != LBM_OK) break;
+    cudaEventRecord(e1, c->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { st = fail(c, LBM_ECUDA, "autotune: %s", cudaGetErrorString(e)); break; }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    c->steps += reps + 2;
+    if (ms < best_ms) { best_ms = ms; best = t; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -687,7 +733,25 @@ lbm_status lbm_autotune(lbm_ctx* c, int reps, long long* choice) {
   drop_graphs(c);
   c->have_u_old = 0;
   if (st != LBM_OK) return st;
-  if (choice) *choice = (long long)best.bx * 1000000 + best.by * 10000 + best.zchunk;
+  if (choice) *choice = tile_code(best);
+  return LBM_OK;
+}
+
+lbm_status lbm_set_tile(lbm_ctx* c, long long code) {
+  LBM_CHECK_CTX(c);
+  for (const TileCfg& t : step_candidates(c)) {
+    if (tile_code(t) == code) {
+      c->step_cfg = t;
+      drop_graphs(c);
+      return LBM_OK;
+    }
+  }
+  return fail(c, LBM_EINVAL, "tile code %lld is not compiled for this precision/stencil", code);
+}
+
+lbm_status lbm_get_tile(const lbm_ctx* c, long long* code) {
+  if (!c || !code) return fail(nullptr, LBM_EINVAL, "null argument");
+  *code = tile_code(c->step_cfg);
   return LBM_OK;
 }
 

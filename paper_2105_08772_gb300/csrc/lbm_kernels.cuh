@@ -118,8 +118,45 @@ __device__ __forceinline__ void load_plane(const LatticeDesc& d, int x0, int y0,
   }
 }
 
-// Shan-Chen force (Eq. (8)) at interior node (tx, ty) of the current plane
-// from the psi ring.  slots[k] is the ring slot of plane z + k - R.
+// Shan-Chen force (Eq. (8)) from psi planes in shared memory.  planes[dz + R]
+// points at the node's own position in the psi plane at offset dz; rows are PX
+// apart.  The stencil is summed in antisymmetric pairs, W (psi(x + xi) -
+// psi(x - xi)) xi, so that the two psi values cancel before they are scaled:
+// a uniform region gives exactly F = 0 and the rounding error scales with F,
+// not with the psi values.  (Summing the 18 terms one by one in raster order
+// lets FP32 rounding build a spurious force that grows the density error of a
+// 1000-step droplet run tenfold.)
+template <typename T, int ST, int PX>
+__device__ __forceinline__ void sc_force_pairs(const T* const* planes, T G, T& Fx, T& Fy, T& Fz) {
+  constexpr int R = stencil_radius<ST>();
+  T sx = 0, sy = 0, sz = 0;
+#pragma unroll
+  for (int dz = 0; dz <= R; ++dz) {
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy) {
+#pragma unroll
+      for (int dx = -R; dx <= R; ++dx) {
+        // one representative per pair: dz > 0, or dz == 0 and (dy > 0 or (dy == 0 and dx > 0))
+        const bool upper = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
+        const double Wd = shell_weight<ST>(dx * dx + dy * dy + dz * dz);
+        if (upper && Wd != 0.0) {
+          const T d = planes[R + dz][dy * PX + dx] - planes[R - dz][-dy * PX - dx];
+          const T Wdiff = (T)Wd * d;
+          if (dx != 0) sx += (T)dx * Wdiff;
+          if (dy != 0) sy += (T)dy * Wdiff;
+          if (dz != 0) sz += (T)dz * Wdiff;
+        }
+      }
+    }
+  }
+  const T k = -G * (T)(1.0 / 3.0) * planes[R][0];
+  Fx = k * sx;
+  Fy = k * sy;
+  Fz = k * sz;
+}
+
+// Force at interior node (tx, ty) of the current plane from the psi ring;
+// slots[k] is the ring slot of plane z + k - R.
 template <int P, int ST, int BX, int BY>
 __device__ __forceinline__ void sc_force(const typename Storage<P>::T* ring, const int* slots, int tx,
                                          int ty, typename Storage<P>::T G,
@@ -128,30 +165,10 @@ __device__ __forceinline__ void sc_force(const typename Storage<P>::T* ring, con
   using Sh = StepShape<P, ST, BX, BY>;
   using T = typename Sh::T;
   constexpr int R = Sh::R, PX = Sh::PX, PY = Sh::PY;
-  T sx = 0, sy = 0, sz = 0;
+  const T* planes[2 * R + 1];
 #pragma unroll
-  for (int dz = -R; dz <= R; ++dz) {
-    const T* pl = ring + slots[dz + R] * (PX * PY);
-#pragma unroll
-    for (int dy = -R; dy <= R; ++dy) {
-#pragma unroll
-      for (int dx = -R; dx <= R; ++dx) {
-        const double Wd = shell_weight<ST>(dx * dx + dy * dy + dz * dz);
-        if (Wd != 0.0 && (dx != 0 || dy != 0 || dz != 0)) {
-          const T p = pl[(ty + R + dy) * PX + (tx + R + dx)];
-          const T Wp = (T)Wd * p;
-          if (dx != 0) sx += (T)dx * Wp;
-          if (dy != 0) sy += (T)dy * Wp;
-          if (dz != 0) sz += (T)dz * Wp;
-        }
-      }
-    }
-  }
-  const T psic = ring[slots[R] * (PX * PY) + (ty + R) * PX + (tx + R)];
-  const T k = -G * (T)(1.0 / 3.0) * psic;
-  Fx = k * sx;
-  Fy = k * sy;
-  Fz = k * sz;
+  for (int k = 0; k <= 2 * R; ++k) planes[k] = ring + slots[k] * (PX * PY) + (ty + R) * PX + (tx + R);
+  sc_force_pairs<T, ST, PX>(planes, G, Fx, Fy, Fz);
 }
 
 // BGK + Guo collision of one node in shifted form, g_i = f_i - w_i n0:
@@ -159,7 +176,11 @@ __device__ __forceinline__ void sc_force(const typename Storage<P>::T* ring, con
 //   g_i^eq = w_i [dn + n (3 e.u + 9/2 (e.u)^2 - 3/2 u.u)]          Eq. (6)
 //   F_i    = (1 - omega/2) w_i [3 e.F + 9 (e.u)(e.F) - 3 u.F]       Eq. (5)
 // Opposite velocities share the even part; the odd part flips sign.
-template <typename T>
+// CLOSE_MASS: the collision conserves mass exactly (sum g*_i = dn); in FP32
+// the rounded weights sum to 1 + 1.5e-8, which would add a systematic
+// 1.5e-8 (n - n0) to every node every step, so the rest population is set to
+// dn - sum_{i>0} g*_i instead (same value in exact arithmetic).
+template <typename T, bool CLOSE_MASS>
 __device__ __forceinline__ void collide(T* g, T dn, T n, T ux, T uy, T uz, T Fx, T Fy, T Fz,
                                         T omega) {
   const T uu = ux * ux + uy * uy + uz * uz;
@@ -177,6 +198,12 @@ __device__ __forceinline__ void collide(T* g, T dn, T n, T ux, T uy, T uz, T Fx,
     const T odd = (T)3 * (omega * n * eu + cg * eF);
     g[i] = om1 * g[i] + wi * (even + odd);
     g[i + 1] = om1 * g[i + 1] + wi * (even - odd);
+  }
+  if (CLOSE_MASS) {
+    T rest = dn;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) rest -= g[i];
+    g[0] = rest;
   }
 }
 
@@ -266,25 +293,33 @@ lattice_kernel(LatticeDesc d, int zchunk, ObsArgs oa) {
       T g[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) g[i] = pk[i * NT + tid];
-      T dn, jx, jy, jz;
-      moments(g, dn, jx, jy, jz);
-      const T n = n0 + dn;
       T Fx, Fy, Fz;
       sc_force<P, ST, BX, BY>(ring, slots, tx, ty, G, Fx, Fy, Fz);
-      const T inv_n = (T)1 / n;
-      const T ux = (jx + (T)0.5 * Fx) * inv_n;
-      const T uy = (jy + (T)0.5 * Fy) * inv_n;
-      const T uz = (jz + (T)0.5 * Fz) * inv_n;
       const int z = z0 + k;
       const long long node = ((long long)z * d.ny + (y0 + ty)) * d.nx + (x0 + tx);
       if (MODE == kModeStep) {
-        collide<T>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, omega);
+        T dn, jx, jy, jz;
+        moments(g, dn, jx, jy, jz);
+        const T n = n0 + dn;
+        const T inv_n = (T)1 / n;
+        const T ux = (jx + (T)0.5 * Fx) * inv_n;
+        const T uy = (jy + (T)0.5 * Fy) * inv_n;
+        const T uz = (jz + (T)0.5 * Fz) * inv_n;
+        collide<T, P != kF64>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, omega);
         S* __restrict__ dst = static_cast<S*>(d.dst);
 #pragma unroll
         for (int i = 0; i < Q; ++i) Storage<P>::store(dst + (long long)i * plane + node, g[i], scale);
       } else {
-        const double nd = (double)n;
-        const double uxd = (double)ux, uyd = (double)uy, uzd = (double)uz;
+        // observables: moments and velocity accumulated in FP64 whatever the storage
+        double gd[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) gd[i] = (double)g[i];
+        double dnd, jxd, jyd, jzd;
+        moments(gd, dnd, jxd, jyd, jzd);
+        const double nd = d.n0 + dnd;
+        const double uxd = (jxd + 0.5 * (double)Fx) / nd;
+        const double uyd = (jyd + 0.5 * (double)Fy) / nd;
+        const double uzd = (jzd + 0.5 * (double)Fz) / nd;
         acc_mass += nd;
         if (!(nd > 0.0) || !isfinite(nd) || !isfinite(uxd) || !isfinite(uyd) || !isfinite(uzd))
           acc_bad += 1.0;

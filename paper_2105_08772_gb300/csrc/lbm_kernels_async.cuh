@@ -1,0 +1,189 @@
+// Pipelined variant of the fused Shan-Chen step (FP32 / FP64 storage).
+//
+// Same arithmetic as lattice_kernel (lbm_kernels.cuh), different data
+// movement.  The pulled populations of a padded plane (tile + R halo) are
+// copied global -> shared with cp.async into one of NS stages, D planes
+// ahead of the plane whose density is being formed, so the HBM reads of the
+// next planes are in flight while the current plane is collided and stored.
+// Stage layout: stage[i][j], j = jy * PX + jx over the padded plane; element
+// (i, j) holds f*_i at the pull source of padded node j, i.e. f_i(x_j, t).
+//
+// Work split: the box is cut into (BX x BY) columns and every column into
+// the same z chunks.  Work items (chunk, column) are numbered with the column
+// fastest and a persistent grid takes them round-robin, so the CTAs resident
+// at any moment work on neighbouring columns at the same z: a halo row one
+// CTA reads from HBM is read by its neighbour while it is still in L2.  The
+// host picks the chunk length that makes the rounds of the grid fullest.
+//
+// Per plane (index qd in a segment, planes z0-R .. z0+zc+R-1):
+//   wait for plane qd's copies; barrier
+//   issue the copies of plane qd + D             (its stage was freed last iteration)
+//   density + psi of plane qd -> psi ring; barrier
+//   collide plane qd - 2R (its pulled populations are in stage (qd - R) % NS)
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <int P, int ST, int BX, int BY, int D>
+struct AsyncShape {
+  using T = typename Storage<P>::T;
+  static constexpr int R = stencil_radius<ST>();
+  static constexpr int PX = BX + 2 * R;
+  static constexpr int PY = BY + 2 * R;
+  static constexpr int NPAD = PX * PY;
+  static constexpr int NT = BX * BY;
+  static constexpr int NS = R + 1 + D;     // population stages
+  static constexpr int NR = 2 * R + 1;     // psi planes
+  static constexpr int NPER = (NPAD + NT - 1) / NT;
+  static constexpr size_t stage_elems = (size_t)Q * NPAD;
+  static constexpr size_t smem_bytes = sizeof(T) * (NS * stage_elems + NR * NPAD);
+};
+
+__device__ __forceinline__ void cp_async_elem4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <int P, int ST, int BX, int BY, int D>
+__global__ void __launch_bounds__(BX * BY)
+lattice_async_kernel(LatticeDesc d, int zchunk) {
+  using Sh = AsyncShape<P, ST, BX, BY, D>;
+  using T = typename Sh::T;
+  using S = typename Storage<P>::S;
+  static_assert(sizeof(S) == sizeof(T), "async path copies stored values unchanged");
+  constexpr int R = Sh::R, PX = Sh::PX, NPAD = Sh::NPAD, NT = Sh::NT, NS = Sh::NS, NR = Sh::NR;
+  constexpr int NPER = Sh::NPER;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* stages = reinterpret_cast<T*>(smem_raw);
+  T* ring = stages + NS * Sh::stage_elems;
+
+  const int nx = d.nx, ny = d.ny, nz = d.nz;
+  const long long plane = d.plane;
+  const S* __restrict__ src = static_cast<const S*>(d.src);
+  S* __restrict__ dst = static_cast<S*>(d.dst);
+  const T n0 = (T)d.n0, G = (T)d.eos.G, omega = (T)d.omega;
+  const int tiles_x = (nx + BX - 1) / BX;
+  const int tid = threadIdx.x;
+  const int tx = tid % BX, ty = tid / BX;
+
+  const int ncols = tiles_x * ((ny + BY - 1) / BY);
+  const int nchunks = (nz + zchunk - 1) / zchunk;
+  const long long items = (long long)ncols * nchunks;
+
+#pragma unroll 1
+  for (long long item = blockIdx.x; item < items; item += gridDim.x) {
+    const int col = (int)(item % ncols);
+    const int z0 = (int)(item / ncols) * zchunk;
+    const int zc = min(zchunk, nz - z0);
+    const int x0 = (col % tiles_x) * BX, y0 = (col / tiles_x) * BY;
+    const int w = min(BX, nx - x0), h = min(BY, ny - y0);
+    const bool active = tx < w && ty < h;
+
+    // per padded node of this thread: wrapped source columns / rows for c = -1, 0, +1
+    int xs[NPER][3];
+    long long yrow[NPER][3];
+    bool valid[NPER];
+#pragma unroll
+    for (int s = 0; s < NPER; ++s) {
+      const int j = tid + s * NT;
+      const int jx = j % PX, jy = j / PX;
+      valid[s] = j < NPAD && jx < w + 2 * R && jy < h + 2 * R;
+      const int gx = wrap(x0 + jx - R, nx), gy = wrap(y0 + (valid[s] ? jy : 0) - R, ny);
+      xs[s][0] = wrap(gx + 1, nx);   // source x for c_x = -1
+      xs[s][1] = gx;
+      xs[s][2] = wrap(gx - 1, nx);   // source x for c_x = +1
+      yrow[s][0] = (long long)wrap(gy + 1, ny) * nx;
+      yrow[s][1] = (long long)gy * nx;
+      yrow[s][2] = (long long)wrap(gy - 1, ny) * nx;
+    }
+    const int nplanes = zc + 2 * R;
+
+    auto issue = [&](int q) {
+      if (q < nplanes) {
+        const int z = wrap(z0 - R + q, nz);
+        const long long zo[3] = {(long long)wrap(z + 1, nz) * ny * nx, (long long)z * ny * nx,
+                                 (long long)wrap(z - 1, nz) * ny * nx};
+        T* st = stages + (q % NS) * Sh::stage_elems;
+#pragma unroll
+        for (int s = 0; s < NPER; ++s) {
+          if (!valid[s]) continue;
+          const int j = tid + s * NT;
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const S* g = src + (long long)i * plane + zo[cz(i) + 1] + yrow[s][cy(i) + 1] + xs[s][cx(i) + 1];
+            if (sizeof(T) == 8)
+              cp_async_elem8(st + i * NPAD + j, g);
+            else
+              cp_async_elem4(st + i * NPAD + j, g);
+          }
+        }
+      }
+      cp_async_commit();
+    };
+
+    __syncthreads();   // the previous segment's readers are done with every stage
+#pragma unroll 1
+    for (int q = 0; q < D; ++q) issue(q);
+
+#pragma unroll 1
+    for (int qd = 0; qd < nplanes; ++qd) {
+      cp_async_wait<D - 1>();
+      __syncthreads();
+      issue(qd + D);
+      {  // density and psi of plane qd
+        const T* st = stages + (qd % NS) * Sh::stage_elems;
+        T* rs = ring + (qd % NR) * NPAD;
+#pragma unroll
+        for (int s = 0; s < NPER; ++s) {
+          if (!valid[s]) continue;
+          const int j = tid + s * NT;
+          T sum = 0;
+#pragma unroll
+          for (int i = 0; i < Q; ++i) sum += st[i * NPAD + j];
+          rs[j] = psi_of<T>(n0 + sum, d.eos);
+        }
+      }
+      __syncthreads();
+      const int k = qd - 2 * R;
+      if (k >= 0 && active) {
+        const T* st = stages + ((qd - R) % NS) * Sh::stage_elems;
+        const int jc = (ty + R) * PX + (tx + R);
+        T g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = st[i * NPAD + jc];
+        // force from the psi ring: ring slot of relative plane (k + dz + R) is (qd - R + dz) % NR
+        const T* planes[2 * R + 1];
+#pragma unroll
+        for (int dz = -R; dz <= R; ++dz) planes[dz + R] = ring + ((qd - R + dz) % NR) * NPAD + jc;
+        T Fx, Fy, Fz;
+        sc_force_pairs<T, ST, PX>(planes, G, Fx, Fy, Fz);
+        T dn, jx, jy, jz;
+        moments(g, dn, jx, jy, jz);
+        const T n = n0 + dn;
+        const T inv_n = (T)1 / n;
+        const T ux = (jx + (T)0.5 * Fx) * inv_n;
+        const T uy = (jy + (T)0.5 * Fy) * inv_n;
+        const T uz = (jz + (T)0.5 * Fz) * inv_n;
+        collide<T, P != kF64>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, omega);
+        const long long node = ((long long)(z0 + k) * ny + (y0 + ty)) * nx + (x0 + tx);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) dst[(long long)i * plane + node] = (S)g[i];
+      }
+    }
+    cp_async_wait_all();
+  }
+}
+
+}  // namespace lbm

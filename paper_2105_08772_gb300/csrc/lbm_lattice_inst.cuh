@@ -2,20 +2,20 @@
 // lbm_lattice_<prec>.cu includes this file for its own storage precision.
 #pragma once
 
+#include "lbm_kernels_async.cuh"
 #include "lbm_launch.h"
 
 namespace lbm {
 
-// zchunk == 0 only sets the kernel's shared-memory attribute (done before
-// any stream capture, since it is not a stream operation)
 template <int P, int ST, int BX, int BY, int MODE>
-static cudaError_t launch_one(const LatticeDesc& d, int zchunk, const ObsArgs& oa,
+static cudaError_t launch_one(const LatticeDesc& d, int zchunk, bool prepare, const ObsArgs& oa,
                               cudaStream_t s) {
   using Sh = StepShape<P, ST, BX, BY>;
   auto kern = lattice_kernel<P, ST, BX, BY, MODE>;
-  if (zchunk == 0)
+  if (prepare)
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Sh::smem_bytes);
+  if (zchunk < 1) return cudaErrorInvalidValue;
   const int tiles = ((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
   const int chunks = (d.nz + zchunk - 1) / zchunk;
   dim3 grid(tiles, chunks);
@@ -23,12 +23,73 @@ static cudaError_t launch_one(const LatticeDesc& d, int zchunk, const ObsArgs& o
   return cudaGetLastError();
 }
 
+// Pipelined step kernel on a persistent grid of (resident CTAs per SM) x SMs.
+// The z chunk minimises rounds x (chunk + 2R): the planes the slowest CTA
+// loads when (chunk, column) items are handed out round-robin.
+template <int P, int ST, int BX, int BY, int D>
+static cudaError_t launch_async(const LatticeDesc& d, bool prepare, cudaStream_t s) {
+  using Sh = AsyncShape<P, ST, BX, BY, D>;
+  auto kern = lattice_async_kernel<P, ST, BX, BY, D>;
+  static int resident = 0;   // CTAs of this kernel on the whole GPU
+  if (prepare || resident == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Sh::smem_bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::NT, Sh::smem_bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    resident = (per_sm > 0 ? per_sm : 1) * sms;
+    if (prepare) return cudaSuccess;
+  }
+  const long long cols = (long long)((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
+  int best_zc = d.nz;
+  long long best_cost = -1;
+  for (int zc = 1; zc <= d.nz; ++zc) {
+    const long long items = cols * ((d.nz + zc - 1) / zc);
+    const long long rounds = (items + resident - 1) / resident;
+    const long long cost = rounds * (zc + 2 * Sh::R);
+    if (best_cost < 0 || cost <= best_cost) {
+      best_cost = cost;
+      best_zc = zc;
+    }
+  }
+  const long long items = cols * ((d.nz + best_zc - 1) / best_zc);
+  const long long grid = items < resident ? items : resident;
+  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, best_zc);
+  return cudaGetLastError();
+}
+
+template <int P, int ST>
+static cudaError_t dispatch_async(const LatticeDesc& d, TileCfg c, cudaStream_t s) {
+  if constexpr (P == kF16) {
+    return cudaErrorInvalidValue;
+  } else {
+    const bool prep = c.prepare;
+    const int depth = c.depth;
+    if (ST == 4) {
+      if (c.bx == 32 && c.by == 8 && depth == 1) return launch_async<P, 4, 32, 8, 1>(d, prep, s);
+      if (c.bx == 32 && c.by == 8 && depth == 2) return launch_async<P, 4, 32, 8, 2>(d, prep, s);
+      if (c.bx == 32 && c.by == 4 && depth == 2) return launch_async<P, 4, 32, 4, 2>(d, prep, s);
+      if (c.bx == 64 && c.by == 4 && depth == 1) return launch_async<P, 4, 64, 4, 1>(d, prep, s);
+    } else {
+      if (c.bx == 32 && c.by == 4 && depth == 1) return launch_async<P, ST, 32, 4, 1>(d, prep, s);
+      if (c.bx == 32 && c.by == 8 && depth == 1) return launch_async<P, ST, 32, 8, 1>(d, prep, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+}
+
 template <int P, int ST, int MODE>
 static cudaError_t dispatch_shape(const LatticeDesc& d, TileCfg c, const ObsArgs& oa,
                                   cudaStream_t s) {
-  if (c.bx == 32 && c.by == 4) return launch_one<P, ST, 32, 4, MODE>(d, c.zchunk, oa, s);
-  if (c.bx == 32 && c.by == 8) return launch_one<P, ST, 32, 8, MODE>(d, c.zchunk, oa, s);
-  if (ST == 4 && c.bx == 64 && c.by == 4) return launch_one<P, 4, 64, 4, MODE>(d, c.zchunk, oa, s);
+  if (c.bx == 32 && c.by == 4) return launch_one<P, ST, 32, 4, MODE>(d, c.zchunk, c.prepare, oa, s);
+  if (c.bx == 32 && c.by == 8) return launch_one<P, ST, 32, 8, MODE>(d, c.zchunk, c.prepare, oa, s);
+  if (ST == 4 && c.bx == 64 && c.by == 4)
+    return launch_one<P, 4, 64, 4, MODE>(d, c.zchunk, c.prepare, oa, s);
   return cudaErrorInvalidValue;
 }
 
@@ -36,6 +97,12 @@ template <int P>
 static cudaError_t dispatch_lattice(int stencil, int mode, const LatticeDesc& d, TileCfg c,
                                     const ObsArgs& oa, cudaStream_t s) {
   if (c.zchunk < 0) return cudaErrorInvalidValue;
+  if (mode == kModeStep && c.kind == 1) {
+    if (stencil == 4) return dispatch_async<P, 4>(d, c, s);
+    if (stencil == 6) return dispatch_async<P, 6>(d, c, s);
+    if (stencil == 8) return dispatch_async<P, 8>(d, c, s);
+    return cudaErrorInvalidValue;
+  }
   if (mode == kModeStep) {
     if (stencil == 4) return dispatch_shape<P, 4, kModeStep>(d, c, oa, s);
     if (stencil == 6) return dispatch_shape<P, 6, kModeStep>(d, c, oa, s);
@@ -43,6 +110,7 @@ static cudaError_t dispatch_lattice(int stencil, int mode, const LatticeDesc& d,
   } else {
     // one shape for the field-observable pass
     TileCfg o{32, 4, c.zchunk};
+    o.prepare = c.prepare;
     if (stencil == 4) return dispatch_shape<P, 4, kModeObs>(d, o, oa, s);
     if (stencil == 6) return dispatch_shape<P, 6, kModeObs>(d, o, oa, s);
     if (stencil == 8) return dispatch_shape<P, 8, kModeObs>(d, o, oa, s);

@@ -9,20 +9,32 @@
 
 namespace lbm {
 
+// Step-kernel configuration.  kind 0: lattice_kernel (register loads), one CTA
+// per (column, chunk of zchunk planes).  kind 1: lattice_async_kernel
+// (cp.async stages, prefetch depth `depth`), persistent balanced grid.
+// prepare = true launches nothing: it sets the kernel's shared-memory limit
+// (and caches the occupancy), which must happen outside any stream capture.
 struct TileCfg {
   int bx, by, zchunk;
+  int kind = 0;
+  int depth = 1;
+  bool prepare = false;
 };
 
-// tile shapes compiled for the step kernel (E4 / wider stencils)
+// tile shapes compiled for the register-load step kernel (E4 / wider stencils)
 constexpr int kNumShapesE4 = 3;
 constexpr int kShapesE4[kNumShapesE4][2] = {{32, 4}, {32, 8}, {64, 4}};
 constexpr int kNumShapesWide = 2;
 constexpr int kShapesWide[kNumShapesWide][2] = {{32, 4}, {32, 8}};
+// (bx, by, depth) compiled for the pipelined step kernel (F32 / F64 storage)
+constexpr int kNumAsyncE4 = 4;
+constexpr int kAsyncE4[kNumAsyncE4][3] = {{32, 8, 1}, {32, 8, 2}, {32, 4, 2}, {64, 4, 1}};
+constexpr int kNumAsyncWide = 2;
+constexpr int kAsyncWide[kNumAsyncWide][3] = {{32, 4, 1}, {32, 8, 1}};
 
 // Launch one step (mode kModeStep) or the field-observable pass (kModeObs)
 // for a lattice of the given precision and stencil.  Returns
-// cudaErrorInvalidValue for a shape that is not compiled.  cfg.zchunk == 0
-// launches nothing and only sets the kernel's shared-memory limit.
+// cudaErrorInvalidValue for a configuration that is not compiled.
 cudaError_t launch_lattice_f64(int stencil, int mode, const LatticeDesc& d, TileCfg cfg,
                                const ObsArgs& oa, cudaStream_t s);
 cudaError_t launch_lattice_f32(int stencil, int mode, const LatticeDesc& d, TileCfg cfg,
@@ -40,7 +52,7 @@ inline cudaError_t launch_lattice(int prec, int stencil, int mode, const Lattice
   return cudaErrorInvalidValue;
 }
 
-// number of CTAs (= FieldPartial records) a lattice launch uses
+// number of CTAs (= FieldPartial records) a kind-0 lattice launch uses
 inline long long lattice_grid_ctas(const LatticeDesc& d, TileCfg cfg) {
   const long long tiles = (long long)((d.nx + cfg.bx - 1) / cfg.bx) * ((d.ny + cfg.by - 1) / cfg.by);
   return tiles * ((d.nz + cfg.zchunk - 1) / cfg.zchunk);

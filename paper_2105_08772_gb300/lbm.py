@@ -137,6 +137,16 @@ def lbm_autotune(ctx, reps: int = 8) -> int:
     return ch.value
 
 
+def lbm_set_tile(ctx, code: int):
+    check(_lib_.lbm_set_tile(ctx, int(code)), ctx)
+
+
+def lbm_get_tile(ctx) -> int:
+    code = C.c_longlong(0)
+    check(_lib_.lbm_get_tile(ctx, C.byref(code)), ctx)
+    return code.value
+
+
 def lbm_storage_params(ctx) -> tuple[float, float]:
     n0 = C.c_double()
     sc = C.c_double()
@@ -242,6 +252,12 @@ class Lattice:
 
     def autotune(self, reps=8) -> int:
         return lbm_autotune(self.ctx, reps)
+
+    def set_tile(self, code: int):
+        lbm_set_tile(self.ctx, code)
+
+    def get_tile(self) -> int:
+        return lbm_get_tile(self.ctx)
 
     def storage_params(self):
         return lbm_storage_params(self.ctx)

@@ -64,27 +64,50 @@ def test_parity_f64_1000_steps(random_state):
     assert np.max(np.abs(lat.get_populations() - ref)) < 1e-11
 
 
-def test_parity_f32_shifted_1000_steps(random_state):
+@pytest.fixture(scope="module")
+def droplet_state():
+    """The paper's workload: a tanh droplet at the flat-interface densities (Eq. (23))."""
+    shape, c = (16, 24, 32), (16, 12, 8)
+    n = lbm3d.drop_density(shape, c, 6.0, 1.8883, 0.1193)
+    f0 = lbm3d.init_from_density(n)
+    return shape, c, f0, lbm3d.run(f0, oracle_model(), 1000)
+
+
+def test_parity_f32_shifted_1000_steps_droplet(droplet_state):
+    shape, c, f0, ref = droplet_state
+    lat = lattice(shape, prec="f32")
+    lat.init_drop(c, 6.0, 1.8883, 0.1193, 1.0)
+    lat.step(1000)
+    rho_ref = lbm3d.density(ref)
+    rel = np.max(np.abs(lat.rho() - rho_ref) / rho_ref)
+    print(f"f32 shifted droplet: max relative density error after 1000 steps {rel:.3e}")
+    assert rel < 1e-4, rel
+
+
+def test_parity_f32_shifted_1000_steps_random_state(random_state):
+    """A noisy far-from-equilibrium state: FP32 rounding is amplified while it separates."""
     f0, ref = random_state
     lat = lattice(SHAPE, prec="f32")
     lat.set_populations(f0)
     lat.step(1000)
     rho_ref = lbm3d.density(ref)
     rel = np.max(np.abs(lat.rho() - rho_ref) / rho_ref)
+    print(f"f32 shifted random state: max relative density error after 1000 steps {rel:.3e}")
     assert rel < 1e-4, rel
 
 
-def test_parity_f16_shifted_1000_steps(random_state):
-    """Half storage rounds each shifted population to 2^-11 relative every step; the bound
-    below is that rounding times the population scale, accumulated over the run."""
-    f0, ref = random_state
-    lat = lattice(SHAPE, prec="f16")
-    lat.set_populations(f0)
+def test_parity_f16_shifted_1000_steps_droplet(droplet_state):
+    """Half storage rounds every shifted population to 2^-11 of its size each step; on the
+    droplet workload this accumulates to a few 1e-3 over 1000 steps (a plain numpy model of
+    the same storage gives 2.4e-3).  Bound: 1e-2."""
+    shape, c, f0, ref = droplet_state
+    lat = lattice(shape, prec="f16")
+    lat.init_drop(c, 6.0, 1.8883, 0.1193, 1.0)
     lat.step(1000)
     rho_ref = lbm3d.density(ref)
     rel = np.max(np.abs(lat.rho() - rho_ref) / rho_ref)
-    print(f"f16 shifted: max relative density error after 1000 steps {rel:.3e}")
-    assert np.isfinite(rel) and rel < 5e-2
+    print(f"f16 shifted droplet: max relative density error after 1000 steps {rel:.3e}")
+    assert np.isfinite(rel) and rel < 1e-2
 
 
 def test_droplet_init_matches_oracle():
