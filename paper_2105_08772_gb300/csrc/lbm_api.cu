@@ -82,7 +82,6 @@ bool valid_stencil(int s) { return s == 4 || s == 6 || s == 8; }
 bool valid_prec(int p) { return p == kF64 || p == kF32 || p == kF16; }
 
 constexpr int kObsBX = 32, kObsBY = 4;
-constexpr size_t kMaxSmemPerCta = 227 * 1024;   // opt-in limit of one CTA on sm_103
 
 int default_obs_zchunk(lbm_box b) { return b.nz < 8 ? b.nz : 8; }
 
@@ -117,8 +116,9 @@ Layout layout_of(lbm_box b, int prec) {
 bool box_ok(lbm_box b, int stencil) {
   const int m = 2 * radius_of(stencil) + 1;
   if (b.nx < m || b.ny < m || b.nz < m) return false;
+  // node offsets inside one population plane are 32-bit in the kernels
   const double n = (double)b.nx * b.ny * b.nz;
-  return n * Q < 9.0e18 && b.nx <= (1 << 20) && b.ny <= (1 << 20) && b.nz <= (1 << 20);
+  return n < 2147483647.0;
 }
 
 LatticeDesc desc_of(const lbm_ctx* c, int src_buf) {
@@ -181,11 +181,9 @@ std::vector<TileCfg> step_candidates(const lbm_ctx* c) {
       TileCfg t{as[k][0], as[k][1], 1};
       t.kind = 1;
       t.depth = as[k][2];
-      // shared memory of the pipelined kernel: (R + 1 + depth) population stages and
-      // 2R + 1 psi planes of the padded tile; skip what does not fit one CTA
-      const size_t pad = (size_t)(t.bx + 2 * R) * (t.by + 2 * R);
-      const size_t smem = storage_bytes(c->prec) * pad * ((R + 1 + t.depth) * Q + 2 * R + 1);
-      if (smem <= kMaxSmemPerCta) out.push_back(t);
+      // skip what does not fit one CTA's shared memory
+      if (async_smem_bytes(storage_bytes(c->prec), R, t.bx, t.by, t.depth) <= kMaxSmemPerCta)
+        out.push_back(t);
     }
   }
   return out;

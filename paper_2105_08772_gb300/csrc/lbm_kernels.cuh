@@ -176,19 +176,23 @@ __device__ __forceinline__ void sc_force(const typename Storage<P>::T* ring, con
 //   g_i^eq = w_i [dn + n (3 e.u + 9/2 (e.u)^2 - 3/2 u.u)]          Eq. (6)
 //   F_i    = (1 - omega/2) w_i [3 e.F + 9 (e.u)(e.F) - 3 u.F]       Eq. (5)
 // Opposite velocities share the even part; the odd part flips sign.
-// CLOSE_MASS: the collision conserves mass exactly (sum g*_i = dn); in FP32
-// the rounded weights sum to 1 + 1.5e-8, which would add a systematic
-// 1.5e-8 (n - n0) to every node every step, so the rest population is set to
-// dn - sum_{i>0} g*_i instead (same value in exact arithmetic).
-template <typename T, bool CLOSE_MASS>
+// CLOSE_MASS: the collision conserves mass exactly (sum g*_i = dn), but the
+// rounded weights do not sum to exactly 1 (FP32: 1 + 1.5e-8), which would
+// add a systematic error proportional to n - n0 to every node every step; the
+// rest population is set to dn - sum_{i>0} g*_i instead (the same value in
+// exact arithmetic), so mass changes only by uncorrelated rounding.
+// UNIT_TAU: tau = 1 (the relaxation time the method uses); then 1 - omega = 0
+// and the post-collision populations depend on the old ones only through n, j.
+template <typename T, bool CLOSE_MASS, bool UNIT_TAU = false>
 __device__ __forceinline__ void collide(T* g, T dn, T n, T ux, T uy, T uz, T Fx, T Fy, T Fz,
-                                        T omega) {
+                                        T omega_in) {
+  const T omega = UNIT_TAU ? (T)1 : omega_in;
   const T uu = ux * ux + uy * uy + uz * uz;
   const T uF = ux * Fx + uy * Fy + uz * Fz;
   const T cg = (T)1 - (T)0.5 * omega;     // 1 - 1/(2 tau)
   const T om1 = (T)1 - omega;
   const T base = omega * (dn - (T)1.5 * n * uu) - (T)3 * cg * uF;
-  g[0] = om1 * g[0] + (T)(1.0 / 3.0) * base;
+  g[0] = UNIT_TAU ? (T)(1.0 / 3.0) * base : om1 * g[0] + (T)(1.0 / 3.0) * base;
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
     const T eu = (T)cx(i) * ux + (T)cy(i) * uy + (T)cz(i) * uz;
@@ -196,8 +200,13 @@ __device__ __forceinline__ void collide(T* g, T dn, T n, T ux, T uy, T uz, T Fx,
     const T wi = (T)wq(i);
     const T even = base + omega * (T)4.5 * n * eu * eu + (T)9 * cg * eu * eF;
     const T odd = (T)3 * (omega * n * eu + cg * eF);
-    g[i] = om1 * g[i] + wi * (even + odd);
-    g[i + 1] = om1 * g[i + 1] + wi * (even - odd);
+    if (UNIT_TAU) {
+      g[i] = wi * (even + odd);
+      g[i + 1] = wi * (even - odd);
+    } else {
+      g[i] = om1 * g[i] + wi * (even + odd);
+      g[i + 1] = om1 * g[i + 1] + wi * (even - odd);
+    }
   }
   if (CLOSE_MASS) {
     T rest = dn;
@@ -305,7 +314,7 @@ lattice_kernel(LatticeDesc d, int zchunk, ObsArgs oa) {
         const T ux = (jx + (T)0.5 * Fx) * inv_n;
         const T uy = (jy + (T)0.5 * Fy) * inv_n;
         const T uz = (jz + (T)0.5 * Fz) * inv_n;
-        collide<T, P != kF64>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, omega);
+        collide<T, true>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, omega);
         S* __restrict__ dst = static_cast<S*>(d.dst);
 #pragma unroll
         for (int i = 0; i < Q; ++i) Storage<P>::store(dst + (long long)i * plane + node, g[i], scale);

@@ -56,7 +56,7 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <int P, int ST, int BX, int BY, int D>
+template <int P, int ST, int BX, int BY, int D, bool UNIT_TAU>
 __global__ void __launch_bounds__(BX * BY)
 lattice_async_kernel(LatticeDesc d, int zchunk) {
   using Sh = AsyncShape<P, ST, BX, BY, D>;
@@ -91,9 +91,10 @@ lattice_async_kernel(LatticeDesc d, int zchunk) {
     const int w = min(BX, nx - x0), h = min(BY, ny - y0);
     const bool active = tx < w && ty < h;
 
-    // per padded node of this thread: wrapped source columns / rows for c = -1, 0, +1
+    // per padded node of this thread: wrapped source columns / row offsets for
+    // c = -1, 0, +1 (offsets inside one population plane fit 32 bits)
     int xs[NPER][3];
-    long long yrow[NPER][3];
+    int yrow[NPER][3];
     bool valid[NPER];
 #pragma unroll
     for (int s = 0; s < NPER; ++s) {
@@ -104,25 +105,24 @@ lattice_async_kernel(LatticeDesc d, int zchunk) {
       xs[s][0] = wrap(gx + 1, nx);   // source x for c_x = -1
       xs[s][1] = gx;
       xs[s][2] = wrap(gx - 1, nx);   // source x for c_x = +1
-      yrow[s][0] = (long long)wrap(gy + 1, ny) * nx;
-      yrow[s][1] = (long long)gy * nx;
-      yrow[s][2] = (long long)wrap(gy - 1, ny) * nx;
+      yrow[s][0] = wrap(gy + 1, ny) * nx;
+      yrow[s][1] = gy * nx;
+      yrow[s][2] = wrap(gy - 1, ny) * nx;
     }
     const int nplanes = zc + 2 * R;
 
     auto issue = [&](int q) {
       if (q < nplanes) {
         const int z = wrap(z0 - R + q, nz);
-        const long long zo[3] = {(long long)wrap(z + 1, nz) * ny * nx, (long long)z * ny * nx,
-                                 (long long)wrap(z - 1, nz) * ny * nx};
+        const int zo[3] = {wrap(z + 1, nz) * ny * nx, z * ny * nx, wrap(z - 1, nz) * ny * nx};
         T* st = stages + (q % NS) * Sh::stage_elems;
 #pragma unroll
         for (int s = 0; s < NPER; ++s) {
-          if (!valid[s]) continue;
+          if (!valid[s]) continue;   // whole warps of the last pass skip
           const int j = tid + s * NT;
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
-            const S* g = src + (long long)i * plane + zo[cz(i) + 1] + yrow[s][cy(i) + 1] + xs[s][cx(i) + 1];
+            const S* g = src + i * plane + (zo[cz(i) + 1] + yrow[s][cy(i) + 1] + xs[s][cx(i) + 1]);
             if (sizeof(T) == 8)
               cp_async_elem8(st + i * NPAD + j, g);
             else
@@ -176,10 +176,10 @@ lattice_async_kernel(LatticeDesc d, int zchunk) {
         const T ux = (jx + (T)0.5 * Fx) * inv_n;
         const T uy = (jy + (T)0.5 * Fy) * inv_n;
         const T uz = (jz + (T)0.5 * Fz) * inv_n;
-        collide<T, P != kF64>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, omega);
-        const long long node = ((long long)(z0 + k) * ny + (y0 + ty)) * nx + (x0 + tx);
+        collide<T, true, UNIT_TAU>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, omega);
+        const int node = ((z0 + k) * ny + (y0 + ty)) * nx + (x0 + tx);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) dst[(long long)i * plane + node] = (S)g[i];
+        for (int i = 0; i < Q; ++i) dst[i * plane + node] = (S)g[i];
       }
     }
     cp_async_wait_all();

@@ -23,14 +23,13 @@ static cudaError_t launch_one(const LatticeDesc& d, int zchunk, bool prepare, co
   return cudaGetLastError();
 }
 
-// Pipelined step kernel on a persistent grid of (resident CTAs per SM) x SMs.
-// The z chunk minimises rounds x (chunk + 2R): the planes the slowest CTA
-// loads when (chunk, column) items are handed out round-robin.
-template <int P, int ST, int BX, int BY, int D>
-static cudaError_t launch_async(const LatticeDesc& d, bool prepare, cudaStream_t s) {
+template <int P, int ST, int BX, int BY, int D, bool UNIT_TAU>
+static cudaError_t launch_async_variant(const LatticeDesc& d, bool prepare, cudaStream_t s) {
   using Sh = AsyncShape<P, ST, BX, BY, D>;
-  auto kern = lattice_async_kernel<P, ST, BX, BY, D>;
-  static int resident = 0;   // CTAs of this kernel on the whole GPU
+  static_assert(Sh::smem_bytes == async_smem_bytes(sizeof(typename Sh::T), Sh::R, BX, BY, D),
+                "host and device disagree on the pipelined kernel's shared memory");
+  auto kern = lattice_async_kernel<P, ST, BX, BY, D, UNIT_TAU>;
+  static int resident = 0;   // CTAs of this kernel resident on the whole GPU
   if (prepare || resident == 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Sh::smem_bytes);
@@ -63,6 +62,21 @@ static cudaError_t launch_async(const LatticeDesc& d, bool prepare, cudaStream_t
   return cudaGetLastError();
 }
 
+// Pipelined step kernel on a persistent grid of (resident CTAs per SM) x SMs.
+// The z chunk minimises rounds x (chunk + 2R): the planes the slowest CTA
+// loads when (chunk, column) items are handed out round-robin.  tau = 1 runs
+// a specialised collision; prepare readies both variants.
+template <int P, int ST, int BX, int BY, int D>
+static cudaError_t launch_async(const LatticeDesc& d, bool prepare, cudaStream_t s) {
+  if (prepare) {
+    cudaError_t e = launch_async_variant<P, ST, BX, BY, D, true>(d, true, s);
+    if (e != cudaSuccess) return e;
+    return launch_async_variant<P, ST, BX, BY, D, false>(d, true, s);
+  }
+  if (d.omega == 1.0) return launch_async_variant<P, ST, BX, BY, D, true>(d, false, s);
+  return launch_async_variant<P, ST, BX, BY, D, false>(d, false, s);
+}
+
 template <int P, int ST>
 static cudaError_t dispatch_async(const LatticeDesc& d, TileCfg c, cudaStream_t s) {
   if constexpr (P == kF16) {
@@ -74,6 +88,7 @@ static cudaError_t dispatch_async(const LatticeDesc& d, TileCfg c, cudaStream_t 
       if (c.bx == 32 && c.by == 8 && depth == 1) return launch_async<P, 4, 32, 8, 1>(d, prep, s);
       if (c.bx == 32 && c.by == 8 && depth == 2) return launch_async<P, 4, 32, 8, 2>(d, prep, s);
       if (c.bx == 32 && c.by == 4 && depth == 2) return launch_async<P, 4, 32, 4, 2>(d, prep, s);
+      if (c.bx == 32 && c.by == 4 && depth == 1) return launch_async<P, 4, 32, 4, 1>(d, prep, s);
       if (c.bx == 64 && c.by == 4 && depth == 1) return launch_async<P, 4, 64, 4, 1>(d, prep, s);
     } else {
       if (c.bx == 32 && c.by == 4 && depth == 1) return launch_async<P, ST, 32, 4, 1>(d, prep, s);

@@ -27,8 +27,8 @@ constexpr int kShapesE4[kNumShapesE4][2] = {{32, 4}, {32, 8}, {64, 4}};
 constexpr int kNumShapesWide = 2;
 constexpr int kShapesWide[kNumShapesWide][2] = {{32, 4}, {32, 8}};
 // (bx, by, depth) compiled for the pipelined step kernel (F32 / F64 storage)
-constexpr int kNumAsyncE4 = 4;
-constexpr int kAsyncE4[kNumAsyncE4][3] = {{32, 8, 1}, {32, 8, 2}, {32, 4, 2}, {64, 4, 1}};
+constexpr int kNumAsyncE4 = 5;
+constexpr int kAsyncE4[kNumAsyncE4][3] = {{32, 8, 1}, {32, 8, 2}, {32, 4, 1}, {32, 4, 2}, {64, 4, 1}};
 constexpr int kNumAsyncWide = 2;
 constexpr int kAsyncWide[kNumAsyncWide][3] = {{32, 4, 1}, {32, 8, 1}};
 
@@ -51,6 +51,13 @@ inline cudaError_t launch_lattice(int prec, int stencil, int mode, const Lattice
   }
   return cudaErrorInvalidValue;
 }
+
+// dynamic shared memory of the pipelined kernel: (R + 1 + depth) population
+// stages and 2R + 1 psi planes of the padded (bx + 2R) x (by + 2R) tile
+constexpr size_t async_smem_bytes(size_t elem, int R, int bx, int by, int depth) {
+  return elem * (size_t)(bx + 2 * R) * (by + 2 * R) * ((R + 1 + depth) * Q + 2 * R + 1);
+}
+constexpr size_t kMaxSmemPerCta = 227 * 1024;   // opt-in limit of one CTA on sm_103
 
 // number of CTAs (= FieldPartial records) a kind-0 lattice launch uses
 inline long long lattice_grid_ctas(const LatticeDesc& d, TileCfg cfg) {
