@@ -232,6 +232,34 @@ const char* lbm_last_error(const lbm_ctx* ctx);
 lbm_status lbm_tolman_fit(const double* R_s, const double* sigma_s, const int* is_bubble,
                           long long m, int quadratic, double* sigma0, double* delta, double* c);
 
+/* ---------------------------------------------------------------- no-allocation variant */
+
+/* Mass and centre of mass of a density field, for callers that cannot allocate
+ * device memory.  The paper has no counterpart to this entry point: it is the
+ * mass / centre-of-mass part of lbm_observables, offered for code that holds a
+ * density field in its own device buffer but may not call cudaMalloc (or ask a
+ * library to) -- e.g. code running inside another framework's memory pool, or
+ * at a point of a pipeline where new allocations are not allowed.
+ *
+ * dev_rho: device array of nx*ny*nz doubles (layout above), read only.
+ * n_ref: the outer density (e.g. lbm_obs.n_out); the centre of mass is that of
+ * n - n_ref with minimum-image displacements about the centre node, as in
+ * lbm_obs.com.  dev_out: device array of 4 doubles, written with
+ * {sum_x n, com_x, com_y, com_z}.  Async on cuda_stream.
+ *
+ * No device memory is allocated: per-block partial sums go to a fixed scratch
+ * array inside the library (160 KiB per device, held until the process exits).
+ * Limit: nx*ny*nz <= 33554432 nodes (4096 partial sums of 8192 nodes); larger
+ * fields, null pointers or sides < 1 return LBM_EINVAL with a message in
+ * lbm_last_error(NULL).  The first call on a device looks up the scratch's
+ * device address with that device current; make that first call before any
+ * stream capture.  Every call shares the one scratch array, which keeps the
+ * last call's partial sums (each call writes every record it reads, so nothing
+ * needs clearing); calls that overlap on the GPU -- on two streams, say --
+ * race on it and must be serialised by the caller. */
+lbm_status lbm_density_moments_noalloc(const double* dev_rho, int nx, int ny, int nz, double n_ref,
+                                       double* dev_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ EXPORTS = (
     "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_run_to_convergence",
     "lbm_observables", "lbm_rho_profile", "lbm_pt_profile", "lbm_sigma_of_R", "lbm_copy_rho",
     "lbm_copy_velocity", "lbm_save", "lbm_load", "lbm_autotune", "lbm_set_tile", "lbm_get_tile",
-    "lbm_storage_params",
+    "lbm_storage_params", "lbm_density_moments_noalloc",
     "lbm_strerror", "lbm_last_error", "lbm_tolman_fit",
 )
 
@@ -94,6 +94,7 @@ def _load():
         "lbm_strerror": (C.c_char_p, [C.c_int]),
         "lbm_last_error": (C.c_char_p, [_P]),
         "lbm_tolman_fit": (C.c_int, [_D, _D, C.POINTER(C.c_int), C.c_longlong, C.c_int, _D, _D, _D]),
+        "lbm_density_moments_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

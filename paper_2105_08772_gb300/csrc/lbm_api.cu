@@ -65,6 +65,15 @@ lbm_status fail(lbm_ctx* c, lbm_status s, const char* fmt, ...) {
   return s;
 }
 
+}  // namespace
+
+namespace lbm {
+// error message of a call that has no context (read with lbm_last_error(NULL))
+void set_global_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace lbm
+
+namespace {
+
 #define LBM_CUDA(ctx, call)                                                              \
   do {                                                                                   \
     cudaError_t e_ = (call);                                                             \

@@ -164,6 +164,15 @@ def lbm_tolman_fit(R_s, sigma_s, is_bubble, quadratic=True) -> tuple[float, floa
     return s0.value, d.value, c.value
 
 
+def lbm_density_moments_noalloc(dev_rho: int, nx: int, ny: int, nz: int, n_ref: float,
+                                dev_out: int, stream: int = 0):
+    """Mass and centre of mass of a device density field (device pointers as ints);
+    allocates no device memory.  Writes {mass, com_x, com_y, com_z} to dev_out."""
+    check(_lib_.lbm_density_moments_noalloc(C.c_void_p(dev_rho), int(nx), int(ny), int(nz),
+                                            float(n_ref), C.c_void_p(dev_out), C.c_void_p(stream)),
+          None)
+
+
 # ---------------------------------------------------------------- convenience object
 
 @dataclass
