@@ -56,6 +56,28 @@ def measured_peak_gbs():
     return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("lbm_common.cuh", "lbm_kernels.cuh", "lbm_kernels_async.cuh", "lbm_lattice_inst.cuh")
+
+
+def measured_traffic(prec):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None
+    when there is none for this precision or the kernel sources changed since."""
+    import hashlib
+    summary = ROOT / "profiles" / f"lattice_async_{prec}_128.md"
+    if not summary.exists():
+        return None
+    fields = {}
+    for line in summary.read_text().splitlines():
+        if ":" in line and not line.startswith(("|", " ", "#")):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    csrc = ROOT / "paper_2105_08772_gb300" / "csrc"
+    h = hashlib.sha256(b"".join((csrc / f).read_bytes() for f in KERNEL_SOURCES)).hexdigest()
+    if fields.get("source_sha256") != h or "traffic_bytes_per_launch" not in fields:
+        return None
+    return int(fields["traffic_bytes_per_launch"])
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
 
@@ -263,13 +285,7 @@ def main():
     avg_launch_s = kern_ms * 1e-3 / n_launch
     bytes_per_launch = BYTES_PER_LU[args.prec] * N
     achieved = bytes_per_launch / avg_launch_s / 1e9
-    traffic = None
-    tr_path = ROOT / "profiles" / f"traffic_step_{args.prec}_128.json"
-    if tr_path.exists():
-        try:
-            traffic = json.loads(tr_path.read_text()).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = measured_traffic(args.prec)
 
     # end to end through the public API with host buffers
     host = []
@@ -323,7 +339,7 @@ def main():
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "kernel": "lattice_kernel (fused pull + psi halo + Guo-BGK + store)",
+                     "kernel": "fused step (pull + on-chip psi halo + SC force + Guo-BGK + store)",
                      "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": len(lats) * N * 8,
