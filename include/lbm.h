@@ -62,7 +62,7 @@ typedef enum {
     LBM_ENOMIN = 6,      /* result status: sigma[R] has no minimum (C / Delta P <= 0) */
     LBM_ECOLLAPSE = 7,   /* result status: |n_in - n_out| below 1e-2 of the initial contrast */
     LBM_EOFFCENTER = 8,  /* result status: a centre-of-mass coordinate is > 1e-3 off centre */
-    LBM_ETIMEOUT = 9     /* reserved for bounded device-side waits */
+    LBM_ETIMEOUT = 9     /* a bounded device-side wait ran out (status bit 4) */
 } lbm_status;
 
 /* psi(n) kinds (Sec. II below Eq. (8); Sec. IV names the first two). */
@@ -94,7 +94,10 @@ typedef struct { int nx, ny, nz; } lbm_box;
 
 /* Observables of one lattice (Sec. III, Sec. IV).  status_bits: bit 0 no
  * minimum of sigma[R], bit 1 collapsed, bit 2 off-centre, bit 3 non-finite
- * field.  criterion: 0 none, 1 the Delta P test fired, 2 the delta-u test. */
+ * field, bit 4 a step kernel's bounded wait for its copies ran out since the
+ * last initialisation (the field is then invalid; lbm_run_to_convergence
+ * returns LBM_ETIMEOUT).  criterion: 0 none, 1 the Delta P test fired, 2 the
+ * delta-u test. */
 typedef struct {
     double n_in, n_out;         /* density at the centre node and the farthest corner       */
     double P_in, P_out, dP;     /* P^xx of Eq. (9) at those nodes; dP = P_in - P_out         */
@@ -210,8 +213,10 @@ lbm_status lbm_load(lbm_ctx* ctx, const char* path);
 lbm_status lbm_autotune(lbm_ctx* ctx, int reps, long long* choice);
 
 /* Select the step kernel's configuration by the code lbm_autotune reports:
- * kind * 10^8 + bx * 10^6 + by * 10^4 + (kind ? prefetch depth : z chunk), kind 0 the
- * register-load kernel, 1 the cp.async-pipelined kernel (F32/F64 storage only).  A code
+ * kind * 10^8 + bx * 10^6 + by * 10^4 + (kind ? z chunk * 10 + prefetch depth : z chunk),
+ * kind 0 the register-load kernel, 1 the cp.async-pipelined kernel, 2 the row-bulk
+ * pipelined kernel (1 and 2: F32/F64 storage only, z chunk 0 = chosen by the
+ * launcher; 2 needs nx % 4 == 0 and nx >= bx + 8).  A code
  * that is not compiled for this context's precision and stencil gives LBM_EINVAL.
  * lbm_get_tile returns the current code.  Results do not depend on the choice. */
 lbm_status lbm_set_tile(lbm_ctx* ctx, long long code);

@@ -34,6 +34,7 @@ struct lbm_ctx {
   PointOut* pts;
   double* dP_prev;
   lbm_obs* obs_dev;
+  int* err_dev;               // set by a kernel whose bounded wait ran out
   double* n_line;
   double* PT_line;
   int line_len;
@@ -100,6 +101,7 @@ long long obs_partials(lbm_box b, int zchunk) {
 }
 
 constexpr size_t kStateDP = 64;     // offsets inside the state block
+constexpr size_t kStateErr = 96;
 constexpr size_t kStateObs = 128;
 static_assert(sizeof(PointOut) <= kStateDP, "PointOut overlaps dP_prev");
 
@@ -147,27 +149,34 @@ LatticeDesc desc_of(const lbm_ctx* c, int src_buf) {
   d.eos.b = c->eos.b;
   d.eos.Rgas = c->eos.Rgas;
   d.eos.T = c->eos.T;
+  d.err = c->err_dev;
   return d;
 }
 
 TileCfg default_tile(lbm_box b, int prec, int stencil) {
   TileCfg t;
   t.zchunk = b.nz < 16 ? b.nz : 16;
-  if (prec == kF16) {   // register-load kernel
-    t.bx = 32;
-    t.by = stencil == 4 ? 8 : 4;
-    return t;
-  }
-  t.kind = 1;           // pipelined kernel
   t.bx = 32;
-  t.by = (prec == kF64 || stencil != 4) ? 4 : 8;
-  t.depth = (stencil == 4 && prec == kF64) ? 2 : 1;
+  t.by = stencil == 4 ? 8 : 4;
+  if (prec == kF16) return t;   // register-load kernel
+  // pipelined kernel with a launcher-chosen z chunk, if one compiled shape fits
+  const int R = stencil == 4 ? 1 : 2;
+  const int by_pref[2] = {(prec == kF64 || stencil != 4) ? 4 : 8, 4};
+  for (int by : by_pref) {
+    if (async_smem_bytes(prec == kF64 ? 8 : 4, R, 32, by, 1) <= kMaxSmemPerCta) {
+      t.kind = 1;
+      t.zchunk = 0;
+      t.by = by;
+      t.depth = 1;
+      return t;
+    }
+  }
   return t;
 }
 
 long long tile_code(const TileCfg& t) {
   return (long long)t.kind * 100000000 + (long long)t.bx * 1000000 + t.by * 10000 +
-         (t.kind == 1 ? t.depth : t.zchunk);
+         (t.kind >= 1 ? t.zchunk * 10 + t.depth : t.zchunk);
 }
 
 // every step configuration compiled for this precision and stencil
@@ -183,16 +192,35 @@ std::vector<TileCfg> step_candidates(const lbm_ctx* c) {
       out.push_back(t);
     }
   if (c->prec != kF16) {
+    const int R = radius_of(c->stencil);
+    const int (*bs)[3] = c->stencil == 4 ? kBulkE4 : kBulkWide;
+    const int nb = c->stencil == 4 ? kNumBulkE4 : kNumBulkWide;
+    for (int k = 0; k < nb; ++k) {
+      // rows must be 16-byte aligned and wrap at most once
+      if (c->box.nx % 4 != 0 || c->box.nx < bs[k][0] + 8) continue;
+      if (bulk_smem_bytes(storage_bytes(c->prec), R, bs[k][0], bs[k][1], bs[k][2]) > kMaxSmemPerCta)
+        continue;
+      for (int zc : {0, 8, 16, 32}) {
+        if (zc > c->box.nz) continue;
+        TileCfg t{bs[k][0], bs[k][1], zc};
+        t.kind = 2;
+        t.depth = bs[k][2];
+        out.push_back(t);
+      }
+    }
     const int (*as)[3] = c->stencil == 4 ? kAsyncE4 : kAsyncWide;
     const int na = c->stencil == 4 ? kNumAsyncE4 : kNumAsyncWide;
-    const int R = radius_of(c->stencil);
     for (int k = 0; k < na; ++k) {
-      TileCfg t{as[k][0], as[k][1], 1};
-      t.kind = 1;
-      t.depth = as[k][2];
       // skip what does not fit one CTA's shared memory
-      if (async_smem_bytes(storage_bytes(c->prec), R, t.bx, t.by, t.depth) <= kMaxSmemPerCta)
+      if (async_smem_bytes(storage_bytes(c->prec), R, as[k][0], as[k][1], as[k][2]) > kMaxSmemPerCta)
+        continue;
+      for (int zc : {0, 8, 16, 32}) {   // 0: the launcher's own choice
+        if (zc > c->box.nz) continue;
+        TileCfg t{as[k][0], as[k][1], zc};
+        t.kind = 1;
+        t.depth = as[k][2];
         out.push_back(t);
+      }
     }
   }
   return out;
@@ -282,6 +310,7 @@ lbm_status observe(lbm_ctx* c, double* rho_out, double* u_out, int write_u_old, 
     fa.have_u_old = c->have_u_old;
     fa.steps = c->steps;
     fa.dP_prev = c->dP_prev;
+    fa.err = c->err_dev;
     fa.obs_out = c->obs_dev;
     LBM_CUDA(c, launch_finalize(fa, c->stream));
   }
@@ -291,6 +320,7 @@ lbm_status observe(lbm_ctx* c, double* rho_out, double* u_out, int write_u_old, 
 lbm_status reset_history(lbm_ctx* c) {
   const double nan = NAN;
   LBM_CUDA(c, cudaMemcpyAsync(c->dP_prev, &nan, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  LBM_CUDA(c, cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->have_u_old = 0;
   c->have_last = 0;
@@ -389,6 +419,7 @@ lbm_status lbm_create(lbm_box box, double tau, double G, lbm_eos eos, int stenci
   c->pts = reinterpret_cast<PointOut*>(p);
   c->dP_prev = reinterpret_cast<double*>(p + kStateDP);
   c->obs_dev = reinterpret_cast<lbm_obs*>(p + kStateObs);
+  c->err_dev = reinterpret_cast<int*>(p + kStateErr);
   p += L.state;
   c->line_len = box.nx / 2 + 1;
   c->n_line = reinterpret_cast<double*>(p);
@@ -573,6 +604,11 @@ lbm_status lbm_run_to_convergence(lbm_ctx* c, long long max_steps, long long che
     done += k;
     st = lbm_observables(c, nullptr);
     if (st != LBM_OK) return st;
+    if (c->last.status_bits & 16u) {
+      if (steps_done) *steps_done = done;
+      if (criterion) *criterion = 0;
+      return fail(c, LBM_ETIMEOUT, "a step kernel's bounded wait for its copies ran out");
+    }
     if (c->last.status_bits & 8u) {
       if (steps_done) *steps_done = done;
       if (criterion) *criterion = 0;

@@ -26,6 +26,20 @@ __host__ __device__ constexpr int cz(int i) {
   constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
   return t[i];
 }
+// the same components for an index known only at run time: component + 1 of
+// velocity i in two bits at bit 2i of a packed constant (no memory access)
+__host__ __device__ constexpr unsigned long long pack_component(int axis) {
+  unsigned long long p = 0;
+  for (int i = 0; i < Q; ++i) {
+    const int c = axis == 0 ? cx(i) : (axis == 1 ? cy(i) : cz(i));
+    p |= (unsigned long long)(c + 1) << (2 * i);
+  }
+  return p;
+}
+__host__ __device__ __forceinline__ int cx_rt(int i) { return (int)((pack_component(0) >> (2 * i)) & 3ull) - 1; }
+__host__ __device__ __forceinline__ int cy_rt(int i) { return (int)((pack_component(1) >> (2 * i)) & 3ull) - 1; }
+__host__ __device__ __forceinline__ int cz_rt(int i) { return (int)((pack_component(2) >> (2 * i)) & 3ull) - 1; }
+
 // D3Q19 weights: 1/3 rest, 1/18 axis, 1/36 diagonal
 __host__ __device__ constexpr double wq(int i) {
   return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
@@ -113,6 +127,7 @@ struct LatticeDesc {
   double n0;            // storage shift (0 for F64)
   double scale;         // storage scale (1 for F64/F32)
   EosParams eos;
+  int* err;             // device flag set by a kernel whose bounded wait ran out (may be null)
 };
 
 __host__ __device__ __forceinline__ int wrap(int g, int n) {

@@ -78,6 +78,18 @@ struct StepShape {
   static constexpr size_t smem_bytes = ring_bytes + pops_bytes;
 };
 
+// sum of the 19 populations of a node as a balanced tree (short dependency
+// chains; the order is fixed so every kernel forms bitwise the same density)
+template <typename T>
+__device__ __forceinline__ T sum19(const T* v) {
+  const T a = (v[0] + v[1]) + (v[2] + v[3]);
+  const T b = (v[4] + v[5]) + (v[6] + v[7]);
+  const T c = (v[8] + v[9]) + (v[10] + v[11]);
+  const T d = (v[12] + v[13]) + (v[14] + v[15]);
+  const T e = (v[16] + v[17]) + v[18];
+  return ((a + b) + (c + d)) + e;
+}
+
 // Pull the 19 populations of every node of one padded plane (tile + R halo),
 // form psi into the ring slot, park the interior populations if asked.
 template <int P, int ST, int BX, int BY>
@@ -105,16 +117,15 @@ __device__ __forceinline__ void load_plane(const LatticeDesc& d, int x0, int y0,
     const int zs[3] = {zp, z, zm};
     const bool interior = keep && jx >= R && jx < R + w && jy >= R && jy < R + h;
     const int li = (jy - R) * BX + (jx - R);
-    T sum = 0;
+    T v[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const long long idx = (long long)i * plane +
                             ((long long)zs[cz(i) + 1] * ny + ys[cy(i) + 1]) * nx + xs[cx(i) + 1];
-      const T v = Storage<P>::load(src + idx, inv_scale);
-      sum += v;
-      if (interior) pops_slot[i * NT + li] = v;
+      v[i] = Storage<P>::load(src + idx, inv_scale);
+      if (interior) pops_slot[i * NT + li] = v[i];
     }
-    ring_slot[jy * PX + jx] = psi_of<T>(n0 + sum, d.eos);
+    ring_slot[jy * PX + jx] = psi_of<T>(n0 + sum19(v), d.eos);
   }
 }
 
@@ -209,27 +220,26 @@ __device__ __forceinline__ void collide(T* g, T dn, T n, T ux, T uy, T uz, T Fx,
     }
   }
   if (CLOSE_MASS) {
-    T rest = dn;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) rest -= g[i];
-    g[0] = rest;
+    // pair sums first (their odd parts cancel), then a balanced tree
+    const T p1 = g[1] + g[2], p2 = g[3] + g[4], p3 = g[5] + g[6];
+    const T p4 = g[7] + g[8], p5 = g[9] + g[10], p6 = g[11] + g[12];
+    const T p7 = g[13] + g[14], p8 = g[15] + g[16], p9 = g[17] + g[18];
+    g[0] = dn - ((((p1 + p2) + (p3 + p4)) + ((p5 + p6) + (p7 + p8))) + p9);
   }
 }
 
+// density and momentum of one node: momentum from the differences of the nine
+// opposite pairs (1,2), (3,4), ..., (17,18) of the population order
 template <typename T>
 __device__ __forceinline__ void moments(const T* g, T& dn, T& jx, T& jy, T& jz) {
-  dn = 0;
-  jx = 0;
-  jy = 0;
-  jz = 0;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) dn += g[i];
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    if (cx(i)) jx += (T)cx(i) * g[i];
-    if (cy(i)) jy += (T)cy(i) * g[i];
-    if (cz(i)) jz += (T)cz(i) * g[i];
-  }
+  dn = sum19(g);
+  const T d12 = g[1] - g[2], d34 = g[3] - g[4], d56 = g[5] - g[6];
+  const T d78 = g[7] - g[8], d910 = g[9] - g[10], d1112 = g[11] - g[12];
+  const T d1314 = g[13] - g[14], d1516 = g[15] - g[16], d1718 = g[17] - g[18];
+  // x: 1 (+), 7 (+), 9 (+), 11 (+), 13 (+); y: 3, 7, 10, 15, 17 (+); z: 5, 11, 14, 15, 18 (+)
+  jx = (d12 + d78) + (d910 + (d1112 + d1314));
+  jy = (d34 + d78) + ((d1516 + d1718) - d910);
+  jz = (d56 + d1112) + ((d1516 - d1718) - d1314);
 }
 
 template <typename T>

@@ -16,10 +16,13 @@
 // host picks the chunk length that makes the rounds of the grid fullest.
 //
 // Per plane (index qd in a segment, planes z0-R .. z0+zc+R-1):
-//   wait for plane qd's copies; barrier
-//   issue the copies of plane qd + D             (its stage was freed last iteration)
-//   density + psi of plane qd -> psi ring; barrier
-//   collide plane qd - 2R (its pulled populations are in stage (qd - R) % NS)
+//   wait for this thread's copies of plane qd; barrier
+//   issue the copies of plane qd + D       (that stage was last read before the barrier)
+//   density + psi of plane qd -> psi ring slot qd % NR; barrier
+//   collide the plane with index qd - R (its psi neighbours qd-2R .. qd are ready)
+// NS = R + 1 + D population stages and NR = 2R + 1 psi slots.  (A variant that
+// collides one plane later needs one barrier per plane but one more stage,
+// which halves the CTAs per SM; it measured slower.)
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -81,6 +84,15 @@ lattice_async_kernel(LatticeDesc d, int zchunk) {
   const int ncols = tiles_x * ((ny + BY - 1) / BY);
   const int nchunks = (nz + zchunk - 1) / zchunk;
   const long long items = (long long)ncols * nchunks;
+  // per-population base pointers, formed once: each copy and store then needs
+  // one 32-bit offset added to a register
+  const S* srcp[Q];
+  S* dstp[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    srcp[i] = src + i * plane;
+    dstp[i] = dst + i * plane;
+  }
 
 #pragma unroll 1
   for (long long item = blockIdx.x; item < items; item += gridDim.x) {
@@ -109,7 +121,7 @@ lattice_async_kernel(LatticeDesc d, int zchunk) {
       yrow[s][1] = gy * nx;
       yrow[s][2] = wrap(gy - 1, ny) * nx;
     }
-    const int nplanes = zc + 2 * R;
+    const int nplanes = zc + 2 * R;   // planes loaded; plane q is z0 - R + q
 
     auto issue = [&](int q) {
       if (q < nplanes) {
@@ -122,7 +134,7 @@ lattice_async_kernel(LatticeDesc d, int zchunk) {
           const int j = tid + s * NT;
 #pragma unroll
           for (int i = 0; i < Q; ++i) {
-            const S* g = src + i * plane + (zo[cz(i) + 1] + yrow[s][cy(i) + 1] + xs[s][cx(i) + 1]);
+            const S* g = srcp[i] + (zo[cz(i) + 1] + yrow[s][cy(i) + 1] + xs[s][cx(i) + 1]);
             if (sizeof(T) == 8)
               cp_async_elem8(st + i * NPAD + j, g);
             else
@@ -149,24 +161,25 @@ lattice_async_kernel(LatticeDesc d, int zchunk) {
         for (int s = 0; s < NPER; ++s) {
           if (!valid[s]) continue;
           const int j = tid + s * NT;
-          T sum = 0;
+          T v[Q];
 #pragma unroll
-          for (int i = 0; i < Q; ++i) sum += st[i * NPAD + j];
-          rs[j] = psi_of<T>(n0 + sum, d.eos);
+          for (int i = 0; i < Q; ++i) v[i] = st[i * NPAD + j];
+          rs[j] = psi_of<T>(n0 + sum19(v), d.eos);
         }
       }
       __syncthreads();
-      const int k = qd - 2 * R;
+      const int qc = qd - R;       // plane collided now; its z is z0 + qc - R
+      const int k = qc - R;
       if (k >= 0 && active) {
-        const T* st = stages + ((qd - R) % NS) * Sh::stage_elems;
+        const T* st = stages + (qc % NS) * Sh::stage_elems;
         const int jc = (ty + R) * PX + (tx + R);
         T g[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) g[i] = st[i * NPAD + jc];
-        // force from the psi ring: ring slot of relative plane (k + dz + R) is (qd - R + dz) % NR
+        // force from the psi ring: plane qc + dz sits in slot (qc + dz) % NR
         const T* planes[2 * R + 1];
 #pragma unroll
-        for (int dz = -R; dz <= R; ++dz) planes[dz + R] = ring + ((qd - R + dz) % NR) * NPAD + jc;
+        for (int dz = -R; dz <= R; ++dz) planes[dz + R] = ring + ((qc + dz) % NR) * NPAD + jc;
         T Fx, Fy, Fz;
         sc_force_pairs<T, ST, PX>(planes, G, Fx, Fy, Fz);
         T dn, jx, jy, jz;
@@ -179,7 +192,7 @@ lattice_async_kernel(LatticeDesc d, int zchunk) {
         collide<T, true, UNIT_TAU>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, omega);
         const int node = ((z0 + k) * ny + (y0 + ty)) * nx + (x0 + tx);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) dst[i * plane + node] = (S)g[i];
+        for (int i = 0; i < Q; ++i) dstp[i][node] = (S)g[i];
       }
     }
     cp_async_wait_all();

@@ -2,7 +2,7 @@
 // lbm_lattice_<prec>.cu includes this file for its own storage precision.
 #pragma once
 
-#include "lbm_kernels_async.cuh"
+#include "lbm_kernels_bulk.cuh"
 #include "lbm_launch.h"
 
 namespace lbm {
@@ -23,58 +23,104 @@ static cudaError_t launch_one(const LatticeDesc& d, int zchunk, bool prepare, co
   return cudaGetLastError();
 }
 
+// (cost model: rounds x (chunk + 2R), the planes the slowest CTA loads when
+// (chunk, column) items are handed out round-robin to `resident` CTAs)
+inline int choose_zchunk(long long cols, int nz, int R, long long resident, int zchunk) {
+  if (zchunk > 0) return zchunk < nz ? zchunk : nz;
+  int best_zc = nz;
+  long long best_cost = -1;
+  for (int zc = 1; zc <= nz; ++zc) {
+    const long long items = cols * ((nz + zc - 1) / zc);
+    const long long rounds = (items + resident - 1) / resident;
+    const long long cost = rounds * (zc + 2 * R);
+    if (best_cost < 0 || cost <= best_cost) {
+      best_cost = cost;
+      best_zc = zc;
+    }
+  }
+  return best_zc;
+}
+
+template <typename Kern>
+static cudaError_t prepare_persistent(Kern kern, int threads, size_t smem, int* resident) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // (the default L1/shared carveout is kept: forcing all of it to shared
+  //  memory measured 1.5x slower -- the element copies profit from L1)
+  int per_sm = 0, dev = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  *resident = (per_sm > 0 ? per_sm : 1) * sms;
+  return cudaSuccess;
+}
+
 template <int P, int ST, int BX, int BY, int D, bool UNIT_TAU>
-static cudaError_t launch_async_variant(const LatticeDesc& d, bool prepare, cudaStream_t s) {
+static cudaError_t launch_async_variant(const LatticeDesc& d, int zchunk, bool prepare,
+                                        cudaStream_t s) {
   using Sh = AsyncShape<P, ST, BX, BY, D>;
   static_assert(Sh::smem_bytes == async_smem_bytes(sizeof(typename Sh::T), Sh::R, BX, BY, D),
                 "host and device disagree on the pipelined kernel's shared memory");
   auto kern = lattice_async_kernel<P, ST, BX, BY, D, UNIT_TAU>;
   static int resident = 0;   // CTAs of this kernel resident on the whole GPU
   if (prepare || resident == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Sh::smem_bytes);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::NT, Sh::smem_bytes);
-    if (e != cudaSuccess) return e;
-    e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    resident = (per_sm > 0 ? per_sm : 1) * sms;
-    if (prepare) return cudaSuccess;
+    cudaError_t e = prepare_persistent(kern, Sh::NT, Sh::smem_bytes, &resident);
+    if (e != cudaSuccess || prepare) return e;
   }
   const long long cols = (long long)((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
-  int best_zc = d.nz;
-  long long best_cost = -1;
-  for (int zc = 1; zc <= d.nz; ++zc) {
-    const long long items = cols * ((d.nz + zc - 1) / zc);
-    const long long rounds = (items + resident - 1) / resident;
-    const long long cost = rounds * (zc + 2 * Sh::R);
-    if (best_cost < 0 || cost <= best_cost) {
-      best_cost = cost;
-      best_zc = zc;
-    }
-  }
-  const long long items = cols * ((d.nz + best_zc - 1) / best_zc);
+  const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
+  const long long items = cols * ((d.nz + zc - 1) / zc);
   const long long grid = items < resident ? items : resident;
-  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, best_zc);
+  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, zc);
   return cudaGetLastError();
 }
 
-// Pipelined step kernel on a persistent grid of (resident CTAs per SM) x SMs.
-// The z chunk minimises rounds x (chunk + 2R): the planes the slowest CTA
-// loads when (chunk, column) items are handed out round-robin.  tau = 1 runs
-// a specialised collision; prepare readies both variants.
-template <int P, int ST, int BX, int BY, int D>
-static cudaError_t launch_async(const LatticeDesc& d, bool prepare, cudaStream_t s) {
-  if (prepare) {
-    cudaError_t e = launch_async_variant<P, ST, BX, BY, D, true>(d, true, s);
-    if (e != cudaSuccess) return e;
-    return launch_async_variant<P, ST, BX, BY, D, false>(d, true, s);
+template <int P, int ST, int BX, int BY, int D, bool UNIT_TAU>
+static cudaError_t launch_bulk_variant(const LatticeDesc& d, int zchunk, bool prepare,
+                                       cudaStream_t s) {
+  using Sh = BulkShape<P, ST, BX, BY, D>;
+  static_assert(Sh::smem_bytes == bulk_smem_bytes(sizeof(typename Sh::T), Sh::R, BX, BY, D),
+                "host and device disagree on the bulk kernel's shared memory");
+  auto kern = lattice_bulk_kernel<P, ST, BX, BY, D, UNIT_TAU>;
+  static int resident = 0;
+  if (prepare || resident == 0) {
+    cudaError_t e = prepare_persistent(kern, Sh::NT, Sh::smem_bytes, &resident);
+    if (e != cudaSuccess || prepare) return e;
   }
-  if (d.omega == 1.0) return launch_async_variant<P, ST, BX, BY, D, true>(d, false, s);
-  return launch_async_variant<P, ST, BX, BY, D, false>(d, false, s);
+  if (d.nx % 4 != 0 || d.nx < Sh::XW) return cudaErrorInvalidValue;
+  const long long cols = (long long)((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
+  const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
+  const long long items = cols * ((d.nz + zc - 1) / zc);
+  const long long grid = items < resident ? items : resident;
+  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, zc);
+  return cudaGetLastError();
+}
+
+template <int P, int ST, int BX, int BY, int D>
+static cudaError_t launch_bulk(const LatticeDesc& d, int zchunk, bool prepare, cudaStream_t s) {
+  if (prepare) {
+    cudaError_t e = launch_bulk_variant<P, ST, BX, BY, D, true>(d, 0, true, s);
+    if (e != cudaSuccess) return e;
+    return launch_bulk_variant<P, ST, BX, BY, D, false>(d, 0, true, s);
+  }
+  if (d.omega == 1.0) return launch_bulk_variant<P, ST, BX, BY, D, true>(d, zchunk, false, s);
+  return launch_bulk_variant<P, ST, BX, BY, D, false>(d, zchunk, false, s);
+}
+
+// Pipelined step kernel on a persistent grid of (resident CTAs per SM) x SMs;
+// tau = 1 runs a specialised collision; prepare readies both variants.
+template <int P, int ST, int BX, int BY, int D>
+static cudaError_t launch_async(const LatticeDesc& d, int zchunk, bool prepare, cudaStream_t s) {
+  if (prepare) {
+    cudaError_t e = launch_async_variant<P, ST, BX, BY, D, true>(d, 0, true, s);
+    if (e != cudaSuccess) return e;
+    return launch_async_variant<P, ST, BX, BY, D, false>(d, 0, true, s);
+  }
+  if (d.omega == 1.0) return launch_async_variant<P, ST, BX, BY, D, true>(d, zchunk, false, s);
+  return launch_async_variant<P, ST, BX, BY, D, false>(d, zchunk, false, s);
 }
 
 template <int P, int ST>
@@ -85,14 +131,32 @@ static cudaError_t dispatch_async(const LatticeDesc& d, TileCfg c, cudaStream_t 
     const bool prep = c.prepare;
     const int depth = c.depth;
     if (ST == 4) {
-      if (c.bx == 32 && c.by == 8 && depth == 1) return launch_async<P, 4, 32, 8, 1>(d, prep, s);
-      if (c.bx == 32 && c.by == 8 && depth == 2) return launch_async<P, 4, 32, 8, 2>(d, prep, s);
-      if (c.bx == 32 && c.by == 4 && depth == 2) return launch_async<P, 4, 32, 4, 2>(d, prep, s);
-      if (c.bx == 32 && c.by == 4 && depth == 1) return launch_async<P, 4, 32, 4, 1>(d, prep, s);
-      if (c.bx == 64 && c.by == 4 && depth == 1) return launch_async<P, 4, 64, 4, 1>(d, prep, s);
+      if (c.bx == 32 && c.by == 8 && depth == 1) return launch_async<P, 4, 32, 8, 1>(d, c.zchunk, prep, s);
+      if (c.bx == 32 && c.by == 8 && depth == 2) return launch_async<P, 4, 32, 8, 2>(d, c.zchunk, prep, s);
+      if (c.bx == 32 && c.by == 4 && depth == 2) return launch_async<P, 4, 32, 4, 2>(d, c.zchunk, prep, s);
+      if (c.bx == 32 && c.by == 4 && depth == 1) return launch_async<P, 4, 32, 4, 1>(d, c.zchunk, prep, s);
+      if (c.bx == 64 && c.by == 4 && depth == 1) return launch_async<P, 4, 64, 4, 1>(d, c.zchunk, prep, s);
     } else {
-      if (c.bx == 32 && c.by == 4 && depth == 1) return launch_async<P, ST, 32, 4, 1>(d, prep, s);
-      if (c.bx == 32 && c.by == 8 && depth == 1) return launch_async<P, ST, 32, 8, 1>(d, prep, s);
+      if (c.bx == 32 && c.by == 4 && depth == 1) return launch_async<P, ST, 32, 4, 1>(d, c.zchunk, prep, s);
+      if (c.bx == 32 && c.by == 8 && depth == 1) return launch_async<P, ST, 32, 8, 1>(d, c.zchunk, prep, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+}
+
+template <int P, int ST>
+static cudaError_t dispatch_bulk(const LatticeDesc& d, TileCfg c, cudaStream_t s) {
+  if constexpr (P == kF16) {
+    return cudaErrorInvalidValue;
+  } else {
+    const bool prep = c.prepare;
+    if (ST == 4) {
+      if (c.bx == 32 && c.by == 8 && c.depth == 1) return launch_bulk<P, 4, 32, 8, 1>(d, c.zchunk, prep, s);
+      if (c.bx == 32 && c.by == 4 && c.depth == 1) return launch_bulk<P, 4, 32, 4, 1>(d, c.zchunk, prep, s);
+      if (c.bx == 64 && c.by == 4 && c.depth == 1) return launch_bulk<P, 4, 64, 4, 1>(d, c.zchunk, prep, s);
+      if (c.bx == 32 && c.by == 8 && c.depth == 2) return launch_bulk<P, 4, 32, 8, 2>(d, c.zchunk, prep, s);
+    } else {
+      if (c.bx == 32 && c.by == 4 && c.depth == 1) return launch_bulk<P, ST, 32, 4, 1>(d, c.zchunk, prep, s);
     }
     return cudaErrorInvalidValue;
   }
@@ -112,6 +176,12 @@ template <int P>
 static cudaError_t dispatch_lattice(int stencil, int mode, const LatticeDesc& d, TileCfg c,
                                     const ObsArgs& oa, cudaStream_t s) {
   if (c.zchunk < 0) return cudaErrorInvalidValue;
+  if (mode == kModeStep && c.kind == 2) {
+    if (stencil == 4) return dispatch_bulk<P, 4>(d, c, s);
+    if (stencil == 6) return dispatch_bulk<P, 6>(d, c, s);
+    if (stencil == 8) return dispatch_bulk<P, 8>(d, c, s);
+    return cudaErrorInvalidValue;
+  }
   if (mode == kModeStep && c.kind == 1) {
     if (stencil == 4) return dispatch_async<P, 4>(d, c, s);
     if (stencil == 6) return dispatch_async<P, 6>(d, c, s);

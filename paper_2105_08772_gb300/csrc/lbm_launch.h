@@ -11,7 +11,10 @@ namespace lbm {
 
 // Step-kernel configuration.  kind 0: lattice_kernel (register loads), one CTA
 // per (column, chunk of zchunk planes).  kind 1: lattice_async_kernel
-// (cp.async stages, prefetch depth `depth`), persistent balanced grid.
+// (cp.async stages, prefetch depth `depth`) on a persistent grid; zchunk 0
+// lets the launcher choose the chunk, > 0 fixes it.  kind 2:
+// lattice_bulk_kernel (row bulk copies), same grid rules; needs nx % 4 == 0
+// and nx >= bx + 8.
 // prepare = true launches nothing: it sets the kernel's shared-memory limit
 // (and caches the occupancy), which must happen outside any stream capture.
 struct TileCfg {
@@ -57,6 +60,20 @@ inline cudaError_t launch_lattice(int prec, int stencil, int mode, const Lattice
 constexpr size_t async_smem_bytes(size_t elem, int R, int bx, int by, int depth) {
   return elem * (size_t)(bx + 2 * R) * (by + 2 * R) * ((R + 1 + depth) * Q + 2 * R + 1);
 }
+// dynamic shared memory of the row-bulk kernel: (R + 1 + depth) stages of
+// 19 x (by + 2R) rows of bx + 8 elements, psi and dn rings of 2R + 1 padded
+// planes, then one 8-byte mbarrier per stage
+constexpr size_t bulk_smem_bytes(size_t elem, int R, int bx, int by, int depth) {
+  return (elem * ((size_t)(R + 1 + depth) * Q * (by + 2 * R) * (bx + 8) +
+                  2 * (size_t)(2 * R + 1) * (bx + 2 * R) * (by + 2 * R)) + 15) / 16 * 16 +
+         8 * (size_t)(R + 1 + depth);
+}
+// (bx, by, depth) compiled for the row-bulk step kernel
+constexpr int kNumBulkE4 = 4;
+constexpr int kBulkE4[kNumBulkE4][3] = {{32, 8, 1}, {32, 4, 1}, {64, 4, 1}, {32, 8, 2}};
+constexpr int kNumBulkWide = 1;
+constexpr int kBulkWide[kNumBulkWide][3] = {{32, 4, 1}};
+
 constexpr size_t kMaxSmemPerCta = 227 * 1024;   // opt-in limit of one CTA on sm_103
 
 // number of CTAs (= FieldPartial records) a kind-0 lattice launch uses
@@ -97,6 +114,7 @@ struct FinalizeArgs {
   int have_u_old;
   long long steps;
   double* dP_prev;        // device: previous Delta P (NaN if none); updated
+  const int* err;         // device: set when a step kernel's bounded wait ran out
   void* obs_out;          // device lbm_obs
 };
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t s);

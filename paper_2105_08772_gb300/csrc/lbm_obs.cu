@@ -135,6 +135,7 @@ __global__ void finalize_kernel(FinalizeArgs a) {
   for (int k = 0; k < 3; ++k)
     if (!(fabs(rel[k]) <= 1e-3)) st |= 4u;
   if (red[6][0] > 0.0 || !isfinite(o.mass)) st |= 8u;
+  if (a.err && *a.err) st |= 16u;
   o.max_u = red[7][0];
   o.du = a.have_u_old ? red[5][0] / V : 0.0;
   const double prev = *a.dP_prev;

@@ -278,3 +278,38 @@ def test_full_size_steps_in_bench_configuration(prec):
         rho_ref = lbm3d.density(ref)
         err = np.max(np.abs(lat.rho() - rho_ref) / rho_ref)
         assert err < (1e-14 if prec == "f64" else 2e-6), (k, err)
+
+
+@pytest.mark.parametrize("prec,code", [(p, c) for p in ("f64", "f32")
+                                       for c in (232080001, 232040001, 264040001, 232080081)]
+                         + [("f32", 232080002)])
+def test_row_bulk_kernel_matches_pipelined_kernel_and_oracle(prec, code):
+    """The row-bulk kernel (kind 2) does the pipelined kernel's arithmetic on the same
+    values: bitwise-equal fields; and it matches the oracle.  nx = 72 with 32-wide tiles
+    has a ragged last column whose staged rows wrap at the right end.  (FP64 with
+    prefetch depth 2 does not fit one CTA's shared memory and is not offered.)"""
+    shape = (13, 22, 72)
+    f0 = inputs.random_populations(shape, seed=21)
+    a = lattice(shape, prec=prec)
+    a.set_populations(f0)
+    a.set_tile(code)
+    a.step(130)
+    b = lattice(shape, prec=prec)
+    b.set_populations(f0)
+    b.set_tile(132080001)
+    b.step(130)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    if prec == "f64":
+        ref = lbm3d.run(f0, oracle_model(), 130)
+        assert np.max(np.abs(a.get_populations() - ref)) < 1e-12
+
+
+def test_row_bulk_kernel_wide_stencil_and_tau():
+    shape = (9, 10, 48)
+    f0 = inputs.random_populations(shape, seed=22)
+    a = lattice(shape, stencil="E6", tau=0.8)
+    a.set_populations(f0)
+    a.set_tile(232040001)
+    a.step(40)
+    ref = lbm3d.run(f0, oracle_model(stencil="E6", tau=0.8), 40)
+    assert np.max(np.abs(a.get_populations() - ref)) < 1e-12
