@@ -50,7 +50,6 @@ extern "C" {
 #endif
 
 typedef struct lbm_ctx lbm_ctx;
-typedef struct lbm_batch lbm_batch;
 
 typedef enum {
     LBM_OK = 0,
@@ -187,6 +186,10 @@ lbm_status lbm_observables(lbm_ctx* ctx, lbm_obs* out);
 lbm_status lbm_rho_profile(lbm_ctx* ctx, double* host_out, long long len);
 lbm_status lbm_pt_profile(lbm_ctx* ctx, double* host_out, long long len);
 
+/* Normal pressure P_N(r) = P^xx(c + r e_x) of Eq. (9) on the same half axis (used by
+ * the flat interface's sigma_0, Eq. (25)).  len = nx/2 + 1.  Synchronises. */
+lbm_status lbm_pn_profile(lbm_ctx* ctx, double* host_out, long long len);
+
 /* Generalised surface tension sigma[R] (Eq. (21)) and its notional derivative
  * [dsigma/dR] (Eq. (22)) at m host radii R[k] > 0, from the last lbm_observables:
  * sigma = dP R/3 + C/R^2 and dsigma = dP/3 - 2C/R^3 + 2D/R^2 (the step P_J
@@ -228,6 +231,23 @@ lbm_status lbm_storage_params(const lbm_ctx* ctx, double* n0, double* scale);
 const char* lbm_strerror(lbm_status s);
 const char* lbm_last_error(const lbm_ctx* ctx);
 
+/* ---------------------------------------------------------------- flat interface */
+
+/* Flat-interface coexistence (Sec. IV, flat-interface paragraph): a strip of gas of
+ * width Lx/2 in liquid (Eq. (24), densities rho_g0 / rho_l0) on a periodic
+ * Lx x m x m box (m = 3 for E4, 5 for E6/E8; a field uniform in y and z is the
+ * paper's 2-D strip reduced exactly), run until delta u < tol_du (checked every
+ * 2^11 steps) or max_steps.  Returns the bulk densities n_g (strip centre) and n_l
+ * (far edge), and sigma_0 = int_{Lx/2}^{Lx} (P_N - P_T) dx (Eq. (25), P from
+ * Eq. (9), trapezoid on the nodes).  The workspace (caller-owned device memory)
+ * holds lbm_flat_workspace_bytes bytes.  Synchronises; LBM_ENOTCONV still fills
+ * the outputs. */
+size_t lbm_flat_workspace_bytes(int Lx, int stencil, int prec);
+lbm_status lbm_flat_interface(double tau, double G, lbm_eos eos, int stencil, int prec, int Lx,
+                              double rho_l0, double rho_g0, long long max_steps, double tol_du,
+                              void* dev_workspace, size_t bytes, void* cuda_stream, double* n_g,
+                              double* n_l, double* sigma0, long long* steps);
+
 /* ---------------------------------------------------------------- Tolman fit */
 
 /* Least-squares fit of Eq. (2) / Eq. (12): sigma_s = sigma0 (1 - 2 delta x + c x^2)
@@ -236,6 +256,39 @@ const char* lbm_last_error(const lbm_ctx* ctx);
  * quadratic = 0 fits the line (c = 0).  Host-only; needs >= 2 (3) usable points. */
 lbm_status lbm_tolman_fit(const double* R_s, const double* sigma_s, const int* is_bubble,
                           long long m, int quadratic, double* sigma0, double* delta, double* c);
+
+/* ---------------------------------------------------------------- batches of lattices */
+
+/* The sweep of Sec. IV (droplets and bubbles of many radii, at several couplings)
+ * as one job: independent lattices of uneven boxes advance together, one launch of
+ * the step kernel per time step for all of them (captured in a CUDA graph of
+ * check_every launches), each until one of the two convergence tests of Sec. IV
+ * holds.  Storage F64 or F32_SHIFTED; every lattice of a batch has the batch's
+ * stencil and precision, and its own box, tau, G and psi.
+ *
+ * lbm_batch_workspace_bytes: device bytes for `slots` resident lattices whose
+ * boxes fit max_box (0 for invalid arguments).  lbm_batch_create: the caller's
+ * workspace (256-byte aligned) and stream, as for lbm_create.  lbm_batch_enqueue:
+ * queue one run (arguments of lbm_create / lbm_init_drop; box <= max_box), *id
+ * receives its index.  lbm_batch_run: run the queue to the end -- a slot takes the
+ * next run when its lattice finishes (converged, max_steps reached, or a non-finite
+ * field); check_every is rounded up to even; *lattice_updates (may be null)
+ * receives the lattice updates done.  Synchronises once per check.
+ * lbm_batch_result: the observables of a finished run (criterion filled in) and
+ * its outcome: LBM_OK (converged), LBM_ENOTCONV, LBM_ENUMERIC, LBM_ETIMEOUT, or the
+ * error that stopped its set-up. */
+typedef struct lbm_batch lbm_batch;
+size_t lbm_batch_workspace_bytes(int slots, lbm_box max_box, int stencil, int prec);
+lbm_status lbm_batch_create(int slots, lbm_box max_box, int stencil, int prec, void* dev_workspace,
+                            size_t bytes, void* cuda_stream, lbm_batch** out);
+lbm_status lbm_batch_enqueue(lbm_batch* b, lbm_box box, double tau, double G, lbm_eos eos,
+                             const double center[3], double R, double rho_in, double rho_out,
+                             double width, int* id);
+lbm_status lbm_batch_run(lbm_batch* b, long long max_steps, long long check_every, double tol_dP_rel,
+                         double tol_du, long long* lattice_updates);
+lbm_status lbm_batch_result(const lbm_batch* b, int id, lbm_obs* out);
+const char* lbm_batch_last_error(const lbm_batch* b);
+void lbm_batch_destroy(lbm_batch* b);
 
 /* ---------------------------------------------------------------- no-allocation variant */
 

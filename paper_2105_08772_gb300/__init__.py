@@ -6,5 +6,6 @@ Secs. II-IV) -- lives in liblbm.so (hand-written CUDA for sm_103a behind the
 C ABI of include/lbm.h).  This package is its Python binding.
 """
 from .lbm import *  # noqa: F401,F403
-from .lbm import Lattice, make_box, make_eos  # noqa: F401
-from ._lib import EXPORTS, LBMError, lbm_obs  # noqa: F401
+from .lbm import Batch, Lattice, make_box, make_eos  # noqa: F401
+from ._lib import (EXPORTS, LBM_EINVAL, LBM_ENOTCONV, LBM_ENUMERIC, LBM_ETIMEOUT, LBM_OK,  # noqa: F401
+                   LBMError, lbm_obs)

@@ -28,7 +28,10 @@ EXPORTS = (
     "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_run_to_convergence",
     "lbm_observables", "lbm_rho_profile", "lbm_pt_profile", "lbm_sigma_of_R", "lbm_copy_rho",
     "lbm_copy_velocity", "lbm_save", "lbm_load", "lbm_autotune", "lbm_set_tile", "lbm_get_tile",
-    "lbm_storage_params", "lbm_density_moments_noalloc",
+    "lbm_storage_params", "lbm_density_moments_noalloc", "lbm_batch_workspace_bytes",
+    "lbm_batch_create", "lbm_batch_enqueue", "lbm_batch_run", "lbm_batch_result",
+    "lbm_batch_last_error", "lbm_batch_destroy", "lbm_pn_profile", "lbm_flat_workspace_bytes",
+    "lbm_flat_interface",
     "lbm_strerror", "lbm_last_error", "lbm_tolman_fit",
 )
 
@@ -95,6 +98,20 @@ def _load():
         "lbm_last_error": (C.c_char_p, [_P]),
         "lbm_tolman_fit": (C.c_int, [_D, _D, C.POINTER(C.c_int), C.c_longlong, C.c_int, _D, _D, _D]),
         "lbm_density_moments_noalloc": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]),
+        "lbm_batch_workspace_bytes": (C.c_size_t, [C.c_int, lbm_box, C.c_int, C.c_int]),
+        "lbm_batch_create": (C.c_int, [C.c_int, lbm_box, C.c_int, C.c_int, _P, C.c_size_t, _P, C.POINTER(_P)]),
+        "lbm_batch_enqueue": (C.c_int, [_P, lbm_box, C.c_double, C.c_double, lbm_eos, _D, C.c_double,
+                                        C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int)]),
+        "lbm_batch_run": (C.c_int, [_P, C.c_longlong, C.c_longlong, C.c_double, C.c_double,
+                                    C.POINTER(C.c_longlong)]),
+        "lbm_batch_result": (C.c_int, [_P, C.c_int, C.POINTER(lbm_obs)]),
+        "lbm_batch_last_error": (C.c_char_p, [_P]),
+        "lbm_batch_destroy": (None, [_P]),
+        "lbm_pn_profile": (C.c_int, [_P, _D, C.c_longlong]),
+        "lbm_flat_workspace_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+        "lbm_flat_interface": (C.c_int, [C.c_double, C.c_double, lbm_eos, C.c_int, C.c_int, C.c_int,
+                                         C.c_double, C.c_double, C.c_longlong, C.c_double, _P,
+                                         C.c_size_t, _P, _D, _D, _D, C.POINTER(C.c_longlong)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -37,6 +37,7 @@ struct lbm_ctx {
   int* err_dev;               // set by a kernel whose bounded wait ran out
   double* n_line;
   double* PT_line;
+  double* PN_line;
   int line_len;
   int cur;                    // buffer holding the current state
   long long steps;
@@ -119,7 +120,7 @@ Layout layout_of(lbm_box b, int prec) {
   L.partials = align256((size_t)L.npart * sizeof(FieldPartial));
   // state block: PointOut at 0, dP_prev at kStateDP, the lbm_obs record at kStateObs
   L.state = align256(kStateObs + sizeof(lbm_obs));
-  L.lines = align256(2 * sizeof(double) * (size_t)(b.nx / 2 + 1));
+  L.lines = align256(3 * sizeof(double) * (size_t)(b.nx / 2 + 1));
   L.total = 2 * L.pop + L.u_old + L.partials + L.state + L.lines;
   return L;
 }
@@ -284,7 +285,8 @@ lbm_status ensure_graph(lbm_ctx* c) {
 
 lbm_status observe(lbm_ctx* c, double* rho_out, double* u_out, int write_u_old, bool finalize) {
   LatticeDesc d = desc_of(c, c->cur);
-  LBM_CUDA(c, launch_point_obs(c->prec, c->stencil, d, c->pts, c->n_line, c->PT_line, c->stream));
+  LBM_CUDA(c, launch_point_obs(c->prec, c->stencil, d, c->pts, c->n_line, c->PT_line, c->PN_line,
+                               c->stream));
   ObsArgs oa;
   oa.n_out = &c->pts->n_out;
   oa.u_old = c->u_old;
@@ -424,6 +426,7 @@ lbm_status lbm_create(lbm_box box, double tau, double G, lbm_eos eos, int stenci
   c->line_len = box.nx / 2 + 1;
   c->n_line = reinterpret_cast<double*>(p);
   c->PT_line = c->n_line + c->line_len;
+  c->PN_line = c->PT_line + c->line_len;
   c->cur = 0;
   c->n0 = 0.0;
   c->scale = 1.0;
@@ -642,6 +645,69 @@ lbm_status lbm_pt_profile(lbm_ctx* c, double* host_out, long long len) {
   return LBM_OK;
 }
 
+lbm_status lbm_pn_profile(lbm_ctx* c, double* host_out, long long len) {
+  LBM_CHECK_CTX(c);
+  if (!host_out || len != c->line_len) return fail(c, LBM_EINVAL, "len must be nx/2 + 1 = %d", c->line_len);
+  if (!c->have_last) return fail(c, LBM_EINVAL, "call lbm_observables first");
+  LBM_CUDA(c, cudaMemcpyAsync(host_out, c->PN_line, len * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+size_t lbm_flat_workspace_bytes(int Lx, int stencil, int prec) {
+  if (!valid_stencil(stencil)) return 0;
+  const int m = 2 * radius_of(stencil) + 1;
+  return lbm_workspace_bytes(lbm_box{Lx, m, m}, stencil, prec);
+}
+
+lbm_status lbm_flat_interface(double tau, double G, lbm_eos eos, int stencil, int prec, int Lx,
+                              double rho_l0, double rho_g0, long long max_steps, double tol_du,
+                              void* dev_workspace, size_t bytes, void* cuda_stream, double* n_g,
+                              double* n_l, double* sigma0, long long* steps) {
+  if (!n_g || !n_l || !sigma0) return fail(nullptr, LBM_EINVAL, "null output pointer");
+  if (!valid_stencil(stencil)) return fail(nullptr, LBM_EINVAL, "stencil must be 4, 6 or 8");
+  if (Lx < 8) return fail(nullptr, LBM_EINVAL, "Lx must be >= 8");
+  if (!(rho_l0 > rho_g0) || !(rho_g0 > 0)) return fail(nullptr, LBM_EINVAL, "need rho_l0 > rho_g0 > 0");
+  const int m = 2 * radius_of(stencil) + 1;
+  const lbm_box box{Lx, m, m};
+  lbm_ctx* c = nullptr;
+  lbm_status st = lbm_create(box, tau, G, eos, stencil, prec, dev_workspace, bytes, cuda_stream, &c);
+  if (st != LBM_OK) return st;
+  // Eq. (24): liquid outside a gas strip of width Lx/2 centred at x0 = Lx/2
+  std::vector<double> rho((size_t)Lx * m * m);
+  const double x0 = 0.5 * Lx, w = 0.5 * Lx, a = 0.5 * (rho_l0 - rho_g0);
+  for (int x = 0; x < Lx; ++x) {
+    const double n = 0.5 * (rho_l0 + rho_g0) - a * tanh(x - (x0 - 0.5 * w)) +
+                     a * (tanh(x - (x0 + 0.5 * w)) + 1.0);
+    for (int k = 0; k < m * m; ++k) rho[(size_t)k * Lx + x] = n;
+  }
+  long long done = 0;
+  int crit = 0;
+  st = lbm_init_rho(c, rho.data());
+  // the flat interface ends at rest: the delta-u test decides (Delta P is zero there)
+  if (st == LBM_OK) st = lbm_run_to_convergence(c, max_steps, 2048, -1.0, tol_du, &done, &crit);
+  if (st == LBM_OK || st == LBM_ENOTCONV) {
+    const lbm_status keep = st;
+    std::vector<double> pt(c->line_len), pn(c->line_len);
+    st = lbm_pt_profile(c, pt.data(), c->line_len);
+    if (st == LBM_OK) st = lbm_pn_profile(c, pn.data(), c->line_len);
+    if (st == LBM_OK) {
+      // Eq. (25) over [Lx/2, Lx]: from the gas centre to the liquid at the far edge
+      double s = 0.0;
+      for (int r = 0; r < c->line_len; ++r)
+        s += ((r == 0 || r == c->line_len - 1) ? 0.5 : 1.0) * (pn[r] - pt[r]);
+      *n_g = c->last.n_in;
+      *n_l = c->last.n_out;
+      *sigma0 = s;
+      if (steps) *steps = done;
+      st = keep;
+    }
+  }
+  if (st != LBM_OK) snprintf(g_err, sizeof(g_err), "%s", c->err);
+  lbm_destroy(c);
+  return st;
+}
+
 lbm_status lbm_sigma_of_R(lbm_ctx* c, const double* R, double* sigma, double* dsigma, long long m) {
   LBM_CHECK_CTX(c);
   if (!c->have_last) return fail(c, LBM_EINVAL, "call lbm_observables first");
@@ -782,14 +848,22 @@ lbm_status lbm_autotune(lbm_ctx* c, int reps, long long* choice) {
 
 lbm_status lbm_set_tile(lbm_ctx* c, long long code) {
   LBM_CHECK_CTX(c);
+  // code = kind 10^8 + bx 10^6 + by 10^4 + (kind ? zchunk 10 + depth : zchunk); any
+  // z chunk in range is accepted for a compiled (kind, bx, by, depth)
+  const int kind = (int)(code / 100000000), bx = (int)(code / 1000000 % 100), by = (int)(code / 10000 % 100);
+  const int low = (int)(code % 10000);
+  const int zc = kind >= 1 ? low / 10 : low, depth = kind >= 1 ? low % 10 : 1;
+  const bool zc_ok = kind >= 1 ? (zc >= 0 && zc <= c->box.nz) : (zc >= 1 && zc <= c->box.nz);
   for (const TileCfg& t : step_candidates(c)) {
-    if (tile_code(t) == code) {
-      c->step_cfg = t;
+    if (zc_ok && t.kind == kind && t.bx == bx && t.by == by && (kind == 0 || t.depth == depth)) {
+      TileCfg chosen = t;
+      chosen.zchunk = zc;
+      c->step_cfg = chosen;
       drop_graphs(c);
       return LBM_OK;
     }
   }
-  return fail(c, LBM_EINVAL, "tile code %lld is not compiled for this precision/stencil", code);
+  return fail(c, LBM_EINVAL, "tile code %lld is not compiled for this precision/stencil/box", code);
 }
 
 lbm_status lbm_get_tile(const lbm_ctx* c, long long* code) {
@@ -866,5 +940,328 @@ lbm_status lbm_tolman_fit(const double* R_s, const double* sigma_s, const int* i
   *cc = quadratic ? a[2] / a[0] : 0.0;
   return LBM_OK;
 }
+
+}  // extern "C"
+
+// ====================================================================== batches
+//
+// Many independent lattices (uneven boxes, each its own G, psi, tau) share one
+// caller-owned workspace cut into equal slots.  Runs wait in a queue; a free
+// slot takes the next run.  Every step advances all active lattices with one
+// launch of the batch kernel (a table of lattices in device memory), captured
+// in a CUDA graph of check_every launches; between graph launches the
+// observables of every active lattice are measured (one synchronisation) and
+// the converged ones free their slots.
+
+#include "lbm_kernels_async.cuh"
+
+namespace {
+
+struct BatchRun {
+  lbm_box box;
+  double tau, G;
+  lbm_eos eos;
+  double center[3], R, rho_in, rho_out, width;
+  int state = 0;            // 0 queued, 1 running, 2 finished
+  lbm_status result = LBM_OK;
+  lbm_obs obs{};
+};
+
+}  // namespace
+
+struct lbm_batch {
+  int slots;
+  lbm_box max_box;
+  int stencil, prec;
+  cudaStream_t stream;
+  cudaStream_t cap_stream;
+  char* ws;
+  size_t slot_bytes;
+  BatchEntry* table_dev;
+  BatchHeader* hdr_dev;
+  std::vector<lbm_ctx*> slot_ctx;
+  std::vector<int> slot_run;
+  std::vector<BatchRun> runs;
+  size_t next_queued = 0;
+  std::vector<BatchEntry> table_host;
+  BatchHeader hdr_host{};
+  std::vector<lbm_obs> obs_host;
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0;
+  int graph_unit_tau = -1;
+  long long lattice_updates = 0;
+  char err[512];
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch* b, lbm_status s, const char* fmt, ...) {
+  char* buf = b ? b->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define LBM_BCUDA(b, call)                                                               \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return bfail((b), LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+struct BatchLayout {
+  size_t slot, table, hdr, total;
+};
+
+BatchLayout batch_layout(int slots, lbm_box max_box, int stencil, int prec) {
+  BatchLayout L;
+  L.slot = lbm_workspace_bytes(max_box, stencil, prec);
+  L.table = align256(sizeof(BatchEntry) * (size_t)slots);
+  L.hdr = align256(sizeof(BatchHeader));
+  L.total = L.slot * (size_t)slots + L.table + L.hdr;
+  return L;
+}
+
+bool batch_unit_tau(const lbm_batch* b) {
+  for (const BatchRun& r : b->runs)
+    if (r.tau != 1.0) return false;
+  return true;
+}
+
+lbm_status batch_fill(lbm_batch* b) {
+  for (int k = 0; k < b->slots; ++k) {
+    while (!b->slot_ctx[k] && b->next_queued < b->runs.size()) {
+      const int id = (int)b->next_queued++;
+      BatchRun& r = b->runs[id];
+      lbm_ctx* c = nullptr;
+      lbm_status st = lbm_create(r.box, r.tau, r.G, r.eos, b->stencil, b->prec, b->ws + k * b->slot_bytes,
+                                 b->slot_bytes, b->stream, &c);
+      if (st == LBM_OK) st = lbm_init_drop(c, r.center, r.R, r.rho_in, r.rho_out, r.width);
+      if (st == LBM_OK) st = lbm_observables(c, &r.obs);   // reference Delta P and velocity
+      if (st != LBM_OK) {
+        r.state = 2;
+        r.result = st;
+        if (c) {
+          snprintf(b->err, sizeof(b->err), "run %d: %s", id, c->err);
+          lbm_destroy(c);
+        } else {
+          snprintf(b->err, sizeof(b->err), "run %d: %s", id, g_err);
+        }
+        if (st == LBM_ECUDA) return st;
+        continue;
+      }
+      r.state = 1;
+      b->slot_ctx[k] = c;
+      b->slot_run[k] = id;
+    }
+  }
+  return LBM_OK;
+}
+
+// table of the active lattices, in slot order, with their global work items
+lbm_status batch_upload(lbm_batch* b) {
+  const TileCfg t = batch_tile(b->prec, b->stencil);
+  b->table_host.clear();
+  long long items = 0;
+  for (int k = 0; k < b->slots; ++k) {
+    lbm_ctx* c = b->slot_ctx[k];
+    if (!c) continue;
+    BatchEntry e;
+    e.d = desc_of(c, 0);
+    e.parity = c->cur;
+    e.zchunk = c->box.nz < 16 ? c->box.nz : 16;
+    e.item_begin = items;
+    items += (long long)((c->box.nx + t.bx - 1) / t.bx) * ((c->box.ny + t.by - 1) / t.by) *
+             ((c->box.nz + e.zchunk - 1) / e.zchunk);
+    b->table_host.push_back(e);
+  }
+  b->hdr_host.n = (int)b->table_host.size();
+  b->hdr_host.total_items = items;
+  if (!b->table_host.empty())
+    LBM_BCUDA(b, cudaMemcpyAsync(b->table_dev, b->table_host.data(),
+                                      sizeof(BatchEntry) * b->table_host.size(), cudaMemcpyHostToDevice,
+                                      b->stream));
+  LBM_BCUDA(b, cudaMemcpyAsync(b->hdr_dev, &b->hdr_host, sizeof(BatchHeader), cudaMemcpyHostToDevice,
+                                    b->stream));
+  LBM_BCUDA(b, cudaStreamSynchronize(b->stream));   // host copies of the table are reused
+  return LBM_OK;
+}
+
+lbm_status batch_graph(lbm_batch* b, int len, bool unit_tau) {
+  if (b->graph && b->graph_len == len && b->graph_unit_tau == (int)unit_tau) return LBM_OK;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  int grid = 0;
+  LBM_BCUDA(b, launch_batch(b->prec, b->stencil, unit_tau, b->table_dev, b->hdr_dev, 0, true, &grid,
+                                 b->stream));
+  cudaGraph_t g = nullptr;
+  LBM_BCUDA(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < len && e == cudaSuccess; ++k)
+    e = launch_batch(b->prec, b->stencil, unit_tau, b->table_dev, b->hdr_dev, k & 1, false, nullptr,
+                     b->cap_stream);
+  cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return bfail(b, LBM_ECUDA, "batch graph capture failed: %s",
+                 cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->graph = nullptr;
+    return bfail(b, LBM_ECUDA, "batch graph instantiate failed: %s", cudaGetErrorString(e));
+  }
+  b->graph_len = len;
+  b->graph_unit_tau = unit_tau;
+  return LBM_OK;
+}
+
+void batch_finish(lbm_batch* b, int k, lbm_status result, int criterion) {
+  BatchRun& r = b->runs[b->slot_run[k]];
+  r.obs = b->slot_ctx[k]->last;
+  r.obs.criterion = criterion;
+  r.result = result;
+  r.state = 2;
+  lbm_destroy(b->slot_ctx[k]);
+  b->slot_ctx[k] = nullptr;
+  b->slot_run[k] = -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_batch_workspace_bytes(int slots, lbm_box max_box, int stencil, int prec) {
+  if (slots < 1 || lbm_workspace_bytes(max_box, stencil, prec) == 0) return 0;
+  if (prec == kF16) return 0;   // batches run the pipelined kernel (FP32 / FP64 storage)
+  return batch_layout(slots, max_box, stencil, prec).total;
+}
+
+lbm_status lbm_batch_create(int slots, lbm_box max_box, int stencil, int prec, void* dev_workspace,
+                            size_t bytes, void* cuda_stream, lbm_batch** out) {
+  if (!out) return bfail(nullptr, LBM_EINVAL, "out is null");
+  *out = nullptr;
+  if (slots < 1) return bfail(nullptr, LBM_EINVAL, "slots must be >= 1");
+  if (!valid_stencil(stencil) || !valid_prec(prec) || prec == kF16)
+    return bfail(nullptr, LBM_EINVAL, "batches need stencil 4/6/8 and F64 or F32 storage");
+  if (!box_ok(max_box, stencil)) return bfail(nullptr, LBM_EINVAL, "max_box too small");
+  const BatchLayout L = batch_layout(slots, max_box, stencil, prec);
+  if (!dev_workspace) return bfail(nullptr, LBM_EINVAL, "workspace is null");
+  if (((uintptr_t)dev_workspace & 255) != 0) return bfail(nullptr, LBM_EINVAL, "workspace not 256-byte aligned");
+  if (bytes < L.total) return bfail(nullptr, LBM_ENOMEM, "workspace has %zu bytes, needs %zu", bytes, L.total);
+  lbm_batch* b = new lbm_batch();
+  b->err[0] = 0;
+  b->slots = slots;
+  b->max_box = max_box;
+  b->stencil = stencil;
+  b->prec = prec;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->ws = static_cast<char*>(dev_workspace);
+  b->slot_bytes = L.slot;
+  b->table_dev = reinterpret_cast<BatchEntry*>(b->ws + L.slot * (size_t)slots);
+  b->hdr_dev = reinterpret_cast<BatchHeader*>(b->ws + L.slot * (size_t)slots + L.table);
+  b->slot_ctx.assign(slots, nullptr);
+  b->slot_run.assign(slots, -1);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete b;
+    return bfail(nullptr, LBM_ECUDA, "cudaStreamCreate failed: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  for (lbm_ctx* c : b->slot_ctx)
+    if (c) lbm_destroy(c);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+lbm_status lbm_batch_enqueue(lbm_batch* b, lbm_box box, double tau, double G, lbm_eos eos,
+                             const double center[3], double R, double rho_in, double rho_out,
+                             double width, int* id) {
+  if (!b) return bfail(nullptr, LBM_EINVAL, "null batch");
+  if (!center || !id) return bfail(b, LBM_EINVAL, "center and id must not be null");
+  if (box.nx > b->max_box.nx || box.ny > b->max_box.ny || box.nz > b->max_box.nz || !box_ok(box, b->stencil))
+    return bfail(b, LBM_EINVAL, "box %dx%dx%d does not fit the batch's slots", box.nx, box.ny, box.nz);
+  BatchRun r;
+  r.box = box;
+  r.tau = tau;
+  r.G = G;
+  r.eos = eos;
+  for (int k = 0; k < 3; ++k) r.center[k] = center[k];
+  r.R = R;
+  r.rho_in = rho_in;
+  r.rho_out = rho_out;
+  r.width = width;
+  b->runs.push_back(r);
+  *id = (int)b->runs.size() - 1;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_run(lbm_batch* b, long long max_steps, long long check_every, double tol_dP_rel,
+                         double tol_du, long long* lattice_updates) {
+  if (!b) return bfail(nullptr, LBM_EINVAL, "null batch");
+  if (max_steps < 0 || check_every < 2) return bfail(b, LBM_EINVAL, "max_steps >= 0, check_every >= 2");
+  const int K = (int)(check_every + (check_every & 1));   // even: a graph keeps every parity
+  const bool unit_tau = batch_unit_tau(b);
+  lbm_status st = batch_fill(b);
+  if (st != LBM_OK) return st;
+  st = batch_graph(b, K, unit_tau);
+  if (st != LBM_OK) return st;
+  for (;;) {
+    int active = 0;
+    for (lbm_ctx* c : b->slot_ctx) active += c != nullptr;
+    if (!active) break;
+    st = batch_upload(b);
+    if (st != LBM_OK) return st;
+    LBM_BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
+    b->obs_host.assign(b->slots, lbm_obs{});
+    for (int k = 0; k < b->slots; ++k) {
+      lbm_ctx* c = b->slot_ctx[k];
+      if (!c) continue;
+      c->steps += K;
+      b->lattice_updates += (long long)K * c->box.nx * c->box.ny * c->box.nz;
+      st = observe(c, nullptr, nullptr, 1, true);
+      if (st != LBM_OK) return bfail(b, st, "%s", c->err);
+      LBM_BCUDA(b, cudaMemcpyAsync(&b->obs_host[k], c->obs_dev, sizeof(lbm_obs), cudaMemcpyDeviceToHost,
+                                        b->stream));
+    }
+    LBM_BCUDA(b, cudaStreamSynchronize(b->stream));
+    for (int k = 0; k < b->slots; ++k) {
+      lbm_ctx* c = b->slot_ctx[k];
+      if (!c) continue;
+      c->last = b->obs_host[k];
+      c->have_u_old = 1;
+      c->have_last = 1;
+      if (c->last.status_bits & 16u) batch_finish(b, k, LBM_ETIMEOUT, 0);
+      else if (c->last.status_bits & 8u) batch_finish(b, k, LBM_ENUMERIC, 0);
+      else if (c->last.dP_rel_change < tol_dP_rel) batch_finish(b, k, LBM_OK, 1);
+      else if (c->last.du < tol_du) batch_finish(b, k, LBM_OK, 2);
+      else if (c->steps >= max_steps) batch_finish(b, k, LBM_ENOTCONV, 0);
+    }
+    st = batch_fill(b);
+    if (st != LBM_OK) return st;
+  }
+  if (lattice_updates) *lattice_updates = b->lattice_updates;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_result(const lbm_batch* b, int id, lbm_obs* out) {
+  if (!b || !out) return bfail(nullptr, LBM_EINVAL, "null argument");
+  if (id < 0 || id >= (int)b->runs.size()) return bfail(nullptr, LBM_EINVAL, "no run %d", id);
+  const BatchRun& r = b->runs[id];
+  if (r.state != 2) return bfail(nullptr, LBM_EINVAL, "run %d has not finished", id);
+  *out = r.obs;
+  return r.result;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : g_err; }
 
 }  // extern "C"

@@ -59,16 +59,16 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// One work item (column col, z chunk starting at z0) of lattice d.
 template <int P, int ST, int BX, int BY, int D, bool UNIT_TAU>
-__global__ void __launch_bounds__(BX * BY)
-lattice_async_kernel(LatticeDesc d, int zchunk) {
+__device__ __forceinline__ void async_process_item(const LatticeDesc& d, int zchunk, long long item,
+                                                   unsigned char* smem_raw) {
   using Sh = AsyncShape<P, ST, BX, BY, D>;
   using T = typename Sh::T;
   using S = typename Storage<P>::S;
   static_assert(sizeof(S) == sizeof(T), "async path copies stored values unchanged");
   constexpr int R = Sh::R, PX = Sh::PX, NPAD = Sh::NPAD, NT = Sh::NT, NS = Sh::NS, NR = Sh::NR;
   constexpr int NPER = Sh::NPER;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stages = reinterpret_cast<T*>(smem_raw);
   T* ring = stages + NS * Sh::stage_elems;
 
@@ -80,12 +80,9 @@ lattice_async_kernel(LatticeDesc d, int zchunk) {
   const int tiles_x = (nx + BX - 1) / BX;
   const int tid = threadIdx.x;
   const int tx = tid % BX, ty = tid / BX;
-
   const int ncols = tiles_x * ((ny + BY - 1) / BY);
-  const int nchunks = (nz + zchunk - 1) / zchunk;
-  const long long items = (long long)ncols * nchunks;
-  // per-population base pointers, formed once: each copy and store then needs
-  // one 32-bit offset added to a register
+  // per-population base pointers: each copy and store then needs one 32-bit
+  // offset added to a register
   const S* srcp[Q];
   S* dstp[Q];
 #pragma unroll
@@ -93,9 +90,8 @@ lattice_async_kernel(LatticeDesc d, int zchunk) {
     srcp[i] = src + i * plane;
     dstp[i] = dst + i * plane;
   }
+  {
 
-#pragma unroll 1
-  for (long long item = blockIdx.x; item < items; item += gridDim.x) {
     const int col = (int)(item % ncols);
     const int z0 = (int)(item / ncols) * zchunk;
     const int zc = min(zchunk, nz - z0);
@@ -196,6 +192,61 @@ lattice_async_kernel(LatticeDesc d, int zchunk) {
       }
     }
     cp_async_wait_all();
+  }
+}
+
+template <int P, int ST, int BX, int BY, int D, bool UNIT_TAU>
+__global__ void __launch_bounds__(BX * BY)
+lattice_async_kernel(LatticeDesc d, int zchunk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ncols = ((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
+  const long long items = (long long)ncols * ((d.nz + zchunk - 1) / zchunk);
+#pragma unroll 1
+  for (long long item = blockIdx.x; item < items; item += gridDim.x)
+    async_process_item<P, ST, BX, BY, D, UNIT_TAU>(d, zchunk, item, smem_raw);
+}
+
+// A batch of independent lattices advanced by one launch: entry e owns global
+// work items [item_begin, item_begin + its items); its current state is in
+// d.src when (parity ^ step) is even and in d.dst otherwise.
+struct BatchEntry {
+  LatticeDesc d;
+  long long item_begin;
+  int zchunk;
+  int parity;
+};
+struct BatchHeader {
+  int n;                 // active entries
+  long long total_items;
+};
+
+// MIXED_TAU: the batch holds tau = 1 and other lattices; each item then takes
+// the collision variant of its own lattice, so every lattice evolves bitwise as
+// it would alone.
+template <int P, int ST, int BX, int BY, int D, bool MIXED_TAU>
+__global__ void __launch_bounds__(BX * BY)
+lattice_async_batch_kernel(const BatchEntry* __restrict__ table, const BatchHeader* __restrict__ hdr,
+                           int step) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = hdr->n;
+  const long long total = hdr->total_items;
+#pragma unroll 1
+  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    int lo = 0, hi = n - 1;          // last entry with item_begin <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (table[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+    }
+    LatticeDesc d = table[lo].d;
+    if ((table[lo].parity ^ step) & 1) {
+      const void* t = d.src;
+      d.src = d.dst;
+      d.dst = const_cast<void*>(t);
+    }
+    if (!MIXED_TAU || d.omega == 1.0)
+      async_process_item<P, ST, BX, BY, D, true>(d, table[lo].zchunk, item - table[lo].item_begin, smem_raw);
+    else
+      async_process_item<P, ST, BX, BY, D, false>(d, table[lo].zchunk, item - table[lo].item_begin, smem_raw);
   }
 }
 

@@ -144,6 +144,47 @@ static cudaError_t dispatch_async(const LatticeDesc& d, TileCfg c, cudaStream_t 
   }
 }
 
+template <int P, int ST, int BX, int BY, int D, bool MIXED_TAU>
+static cudaError_t launch_batch_variant(const BatchEntry* table, const BatchHeader* hdr, int step,
+                                        bool prepare, int* grid, cudaStream_t s) {
+  using Sh = AsyncShape<P, ST, BX, BY, D>;
+  auto kern = lattice_async_batch_kernel<P, ST, BX, BY, D, MIXED_TAU>;
+  static int resident = 0;
+  if (prepare || resident == 0) {
+    cudaError_t e = prepare_persistent(kern, Sh::NT, Sh::smem_bytes, &resident);
+    if (e != cudaSuccess) return e;
+  }
+  if (grid) *grid = resident;
+  if (prepare) return cudaSuccess;
+  kern<<<(unsigned)resident, Sh::NT, Sh::smem_bytes, s>>>(table, hdr, step);
+  return cudaGetLastError();
+}
+
+// batches use the pipelined kernel: 32 x 8 tiles for FP32 E4, 32 x 4 otherwise
+template <int P, int ST>
+static cudaError_t dispatch_batch(bool unit_tau, const BatchEntry* table, const BatchHeader* hdr,
+                                  int step, bool prepare, int* grid, cudaStream_t s) {
+  if constexpr (P == kF16) {
+    return cudaErrorInvalidValue;
+  } else if constexpr (P == kF32 && ST == 4) {
+    if (unit_tau) return launch_batch_variant<P, ST, 32, 8, 1, false>(table, hdr, step, prepare, grid, s);
+    return launch_batch_variant<P, ST, 32, 8, 1, true>(table, hdr, step, prepare, grid, s);
+  } else {
+    if (unit_tau) return launch_batch_variant<P, ST, 32, 4, 1, false>(table, hdr, step, prepare, grid, s);
+    return launch_batch_variant<P, ST, 32, 4, 1, true>(table, hdr, step, prepare, grid, s);
+  }
+}
+
+template <int P>
+static cudaError_t dispatch_batch_stencil(int stencil, bool unit_tau, const BatchEntry* table,
+                                          const BatchHeader* hdr, int step, bool prepare, int* grid,
+                                          cudaStream_t s) {
+  if (stencil == 4) return dispatch_batch<P, 4>(unit_tau, table, hdr, step, prepare, grid, s);
+  if (stencil == 6) return dispatch_batch<P, 6>(unit_tau, table, hdr, step, prepare, grid, s);
+  if (stencil == 8) return dispatch_batch<P, 8>(unit_tau, table, hdr, step, prepare, grid, s);
+  return cudaErrorInvalidValue;
+}
+
 template <int P, int ST>
 static cudaError_t dispatch_bulk(const LatticeDesc& d, TileCfg c, cudaStream_t s) {
   if constexpr (P == kF16) {

@@ -82,6 +82,27 @@ inline long long lattice_grid_ctas(const LatticeDesc& d, TileCfg cfg) {
   return tiles * ((d.nz + cfg.zchunk - 1) / cfg.zchunk);
 }
 
+// ---------------------------------------------------------------- batches
+struct BatchEntry;
+struct BatchHeader;
+// the tile every batch of this precision / stencil uses, and its launch;
+// prepare readies the kernel outside capture and reports the grid it uses
+inline TileCfg batch_tile(int prec, int stencil) {
+  TileCfg t{32, (prec == kF32 && stencil == 4) ? 8 : 4, 0};
+  t.kind = 1;
+  return t;
+}
+cudaError_t launch_batch_f64(int stencil, bool unit_tau, const BatchEntry* table, const BatchHeader* hdr,
+                             int step, bool prepare, int* grid, cudaStream_t s);
+cudaError_t launch_batch_f32(int stencil, bool unit_tau, const BatchEntry* table, const BatchHeader* hdr,
+                             int step, bool prepare, int* grid, cudaStream_t s);
+inline cudaError_t launch_batch(int prec, int stencil, bool unit_tau, const BatchEntry* table,
+                                const BatchHeader* hdr, int step, bool prepare, int* grid, cudaStream_t s) {
+  if (prec == kF64) return launch_batch_f64(stencil, unit_tau, table, hdr, step, prepare, grid, s);
+  if (prec == kF32) return launch_batch_f32(stencil, unit_tau, table, hdr, step, prepare, grid, s);
+  return cudaErrorInvalidValue;
+}
+
 // ---------------------------------------------------------------- io / init (lbm_io.cu)
 struct DropInit {
   double cx, cy, cz, R, rho_in, rho_out, width;
@@ -98,9 +119,9 @@ cudaError_t launch_get_plane(int prec, const LatticeDesc& d, int i, double* f_de
 struct PointOut {
   double n_in, n_out, P_in, P_out;
 };
-// centre node, farthest corner and the +x half axis: n, P^xx, P^yy (Eq. (9))
+// centre node, farthest corner and the +x half axis: n, P^yy, P^xx (Eq. (9))
 cudaError_t launch_point_obs(int prec, int stencil, const LatticeDesc& d, PointOut* pts,
-                             double* n_line, double* PT_line, cudaStream_t s);
+                             double* n_line, double* PT_line, double* PN_line, cudaStream_t s);
 
 struct FinalizeArgs {
   const FieldPartial* partials;

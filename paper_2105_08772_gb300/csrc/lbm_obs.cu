@@ -4,7 +4,8 @@
 // Point pass (one thread per sampled node): n and P^xx, P^yy of Eq. (9)
 //   P^{mu nu}(x) = n c_s^2 delta + (G c_s^2 / 2) psi(x) sum_a W_a psi(x + xi_a) xi_a^mu xi_a^nu
 // at the centre node c (P_in), the farthest corner (P_out) and along the +x
-// half axis c + r e_x, r = 0..nx/2 (P_T(r) = P^yy, Sec. III below Eq. (22)).
+// half axis c + r e_x, r = 0..nx/2 (P_T(r) = P^yy, Sec. III below Eq. (22);
+// P_N(r) = P^xx, used by the flat interface's sigma_0, Eq. (25)).
 //
 // Finalize (one CTA, fixed reduction order, so the result is deterministic):
 //   mass M, centre of mass of n - n_out, delta u (Sec. IV), max |u|,
@@ -40,7 +41,7 @@ __device__ double density_at(const LatticeDesc& d, int x, int y, int z) {
 
 template <int P, int ST>
 __global__ void point_obs_kernel(LatticeDesc d, PointOut* pts, double* n_line, double* PT_line,
-                                 int line_len) {
+                                 double* PN_line, int line_len) {
   constexpr int R = stencil_radius<ST>();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 + line_len) return;
@@ -74,7 +75,7 @@ __global__ void point_obs_kernel(LatticeDesc d, PointOut* pts, double* n_line, d
   const double Pyy = n * (1.0 / 3.0) + k * syy;
   if (t == 0) { pts->n_in = n; pts->P_in = Pxx; }
   else if (t == 1) { pts->n_out = n; pts->P_out = Pxx; }
-  else { n_line[t - 2] = n; PT_line[t - 2] = Pyy; }
+  else { n_line[t - 2] = n; PT_line[t - 2] = Pyy; PN_line[t - 2] = Pxx; }
 }
 
 __global__ void finalize_kernel(FinalizeArgs a) {
@@ -150,11 +151,12 @@ __global__ void finalize_kernel(FinalizeArgs a) {
 }  // namespace
 
 cudaError_t launch_point_obs(int prec, int stencil, const LatticeDesc& d, PointOut* pts,
-                             double* n_line, double* PT_line, cudaStream_t s) {
+                             double* n_line, double* PT_line, double* PN_line, cudaStream_t s) {
   const int line_len = d.nx / 2 + 1;
   const int n = 2 + line_len;
   const dim3 grid((n + 63) / 64);
-#define LBM_POINT(PR, STC) point_obs_kernel<PR, STC><<<grid, 64, 0, s>>>(d, pts, n_line, PT_line, line_len)
+#define LBM_POINT(PR, STC) \
+  point_obs_kernel<PR, STC><<<grid, 64, 0, s>>>(d, pts, n_line, PT_line, PN_line, line_len)
   if (stencil != 4 && stencil != 6 && stencil != 8) return cudaErrorInvalidValue;
   switch (prec) {
     case kF64: if (stencil == 4) LBM_POINT(kF64, 4); else if (stencil == 6) LBM_POINT(kF64, 6); else LBM_POINT(kF64, 8); break;

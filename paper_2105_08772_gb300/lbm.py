@@ -173,6 +173,131 @@ def lbm_density_moments_noalloc(dev_rho: int, nx: int, ny: int, nz: int, n_ref: 
           None)
 
 
+def lbm_pn_profile(ctx, length: int) -> np.ndarray:
+    out = np.empty(length)
+    check(_lib_.lbm_pn_profile(ctx, _dptr(out), length), ctx)
+    return out
+
+
+def lbm_flat_workspace_bytes(Lx: int, stencil: int, prec: int) -> int:
+    return int(_lib_.lbm_flat_workspace_bytes(int(Lx), int(stencil), int(prec)))
+
+
+def lbm_flat_interface(tau, G, eos, stencil, prec, Lx, rho_l0, rho_g0, max_steps, tol_du,
+                       dev_workspace: int, nbytes: int, stream: int):
+    """(status, n_g, n_l, sigma0, steps); LBM_ENOTCONV is returned, not raised."""
+    ng, nl, s0, steps = C.c_double(), C.c_double(), C.c_double(), C.c_longlong()
+    st = _lib_.lbm_flat_interface(float(tau), float(G), eos, int(stencil), int(prec), int(Lx),
+                                  float(rho_l0), float(rho_g0), int(max_steps), float(tol_du),
+                                  C.c_void_p(dev_workspace), C.c_size_t(nbytes), C.c_void_p(stream),
+                                  C.byref(ng), C.byref(nl), C.byref(s0), C.byref(steps))
+    if st not in (_lib.LBM_OK, _lib.LBM_ENOTCONV):
+        check(st, None)
+    return st, ng.value, nl.value, s0.value, steps.value
+
+
+def flat_interface(G, psi="one_minus_exp", stencil="E4", prec="f64", tau=1.0, Lx=100, rho_l0=None,
+                   rho_g0=None, max_steps=400_000, tol_du=1e-13, cs_T=0.0):
+    """Flat-interface coexistence on the GPU with a torch-owned workspace.
+    Returns (status, n_g, n_l, sigma0, steps)."""
+    import torch
+    st_, pr = STENCILS[stencil], PRECS[prec]
+    nbytes = lbm_flat_workspace_bytes(Lx, st_, pr)
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    ptr = ws.data_ptr() + (-ws.data_ptr()) % 256
+    rl = 2.0 if rho_l0 is None else rho_l0
+    rg = 0.15 if rho_g0 is None else rho_g0
+    return lbm_flat_interface(tau, G, make_eos(psi, T=cs_T), st_, pr, Lx, rl, rg, max_steps, tol_du, ptr,
+                              nbytes, torch.cuda.current_stream().cuda_stream)
+
+
+# ---------------------------------------------------------------- batches
+
+def _bcheck(status: int, b) -> int:
+    if status != _lib.LBM_OK:
+        raise LBMError(status, _lib_.lbm_batch_last_error(b).decode())
+    return status
+
+
+def lbm_batch_workspace_bytes(slots: int, max_box: lbm_box, stencil: int, prec: int) -> int:
+    return int(_lib_.lbm_batch_workspace_bytes(int(slots), max_box, int(stencil), int(prec)))
+
+
+def lbm_batch_create(slots, max_box, stencil, prec, dev_workspace: int, nbytes: int, stream: int):
+    out = C.c_void_p()
+    _bcheck(_lib_.lbm_batch_create(int(slots), max_box, int(stencil), int(prec), C.c_void_p(dev_workspace),
+                                   C.c_size_t(nbytes), C.c_void_p(stream), C.byref(out)), None)
+    return out
+
+
+def lbm_batch_enqueue(b, box, tau, G, eos, center, R, rho_in, rho_out, width=1.0) -> int:
+    c = np.ascontiguousarray(center, dtype=np.float64)
+    rid = C.c_int(-1)
+    _bcheck(_lib_.lbm_batch_enqueue(b, box, float(tau), float(G), eos, _dptr(c), float(R), float(rho_in),
+                                    float(rho_out), float(width), C.byref(rid)), b)
+    return rid.value
+
+
+def lbm_batch_run(b, max_steps=50_000, check_every=2048, tol_dP_rel=1e-5, tol_du=1e-12) -> int:
+    lu = C.c_longlong(0)
+    _bcheck(_lib_.lbm_batch_run(b, int(max_steps), int(check_every), float(tol_dP_rel), float(tol_du),
+                                C.byref(lu)), b)
+    return lu.value
+
+
+def lbm_batch_result(b, rid: int):
+    """(status, lbm_obs) of a finished run; the status is returned, not raised."""
+    o = lbm_obs()
+    st = _lib_.lbm_batch_result(b, int(rid), C.byref(o))
+    if st == _lib.LBM_EINVAL:
+        _bcheck(st, None)
+    return st, o
+
+
+def lbm_batch_destroy(b) -> None:
+    _lib_.lbm_batch_destroy(b)
+
+
+class Batch:
+    """A batch of lattices on a torch-owned workspace (see lbm_batch_* in include/lbm.h)."""
+
+    def __init__(self, slots: int, max_box, stencil="E4", prec="f32", stream=None):
+        import torch
+        self.max_box = make_box(*max_box)
+        st, pr = STENCILS[stencil], PRECS[prec]
+        self.nbytes = lbm_batch_workspace_bytes(slots, self.max_box, st, pr)
+        if self.nbytes == 0:
+            raise LBMError(_lib.LBM_EINVAL, "invalid batch arguments")
+        self.workspace = torch.empty(self.nbytes + 256, dtype=torch.uint8, device="cuda")
+        ptr = self.workspace.data_ptr()
+        ptr += (-ptr) % 256
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.b = lbm_batch_create(slots, self.max_box, st, pr, ptr, self.nbytes, s.cuda_stream)
+
+    def enqueue(self, box, tau=1.0, G=-5.0, psi="one_minus_exp", center=None, R=8.0, rho_in=2.0,
+                rho_out=0.15, width=1.0, cs_T=0.0) -> int:
+        bx = make_box(*box)
+        c = center if center is not None else (box[0] // 2, box[1] // 2, box[2] // 2)
+        return lbm_batch_enqueue(self.b, bx, tau, G, make_eos(psi, T=cs_T), c, R, rho_in, rho_out, width)
+
+    def run(self, **kw) -> int:
+        return lbm_batch_run(self.b, **kw)
+
+    def result(self, rid: int):
+        return lbm_batch_result(self.b, rid)
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------- convenience object
 
 @dataclass
@@ -255,6 +380,9 @@ class Lattice:
 
     def pt_profile(self) -> np.ndarray:
         return lbm_pt_profile(self.ctx, self.nx // 2 + 1)
+
+    def pn_profile(self) -> np.ndarray:
+        return lbm_pn_profile(self.ctx, self.nx // 2 + 1)
 
     def sigma_of_R(self, R):
         return lbm_sigma_of_R(self.ctx, R)

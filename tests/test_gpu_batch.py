@@ -1,0 +1,69 @@
+"""Batches of lattices (lbm_batch_*): every lattice of a batch evolves exactly as the
+same lattice run alone with the batch's tile, slots are refilled from the queue, and
+small droplets converge by one of the Sec. IV criteria."""
+import numpy as np
+import pytest
+
+import paper_2105_08772_gb300 as P
+
+pytestmark = pytest.mark.gpu
+
+STATE_KEYS = ("n_in", "n_out", "P_in", "P_out", "dP", "mass", "R_e", "C", "D", "R_s", "max_u")
+
+RUNS = [  # box, tau, G, R, rho_in, rho_out
+    ((24, 24, 24), 1.0, -5.0, 6.0, 1.89, 0.12),
+    ((40, 32, 28), 1.0, -5.5, 7.0, 0.12, 1.89),     # bubble
+    ((33, 27, 35), 1.3, -5.5, 6.5, 1.90, 0.12),     # odd sizes, tau != 1
+    ((48, 48, 48), 1.0, -4.6, 11.0, 1.70, 0.25),
+    ((16, 20, 12), 1.0, -5.0, 4.0, 1.89, 0.12),
+]
+
+
+@pytest.mark.parametrize("prec,tile", [("f32", 132080161), ("f64", 132040161)])
+def test_batch_equals_single_lattice_runs(prec, tile):
+    steps, check = 512, 256
+    b = P.Batch(2, (48, 48, 48), prec=prec)
+    ids = [b.enqueue(box, tau=tau, G=G, R=R, rho_in=ri, rho_out=ro) for box, tau, G, R, ri, ro in RUNS]
+    b.run(max_steps=steps, check_every=check, tol_dP_rel=-1.0, tol_du=-1.0)
+    for rid, (box, tau, G, R, ri, ro) in zip(ids, RUNS):
+        st, ob = b.result(rid)
+        assert st == P._lib.LBM_ENOTCONV and ob.steps == steps, (rid, st, ob.steps)
+        lat = P.Lattice(*box, tau=tau, G=G, prec=prec)
+        lat.set_tile(tile - 160 + 10 * min(16, box[2]))   # the batch's z chunk: min(16, nz)
+        lat.init_drop((box[0] // 2, box[1] // 2, box[2] // 2), R, ri, ro)
+        lat.step(steps)
+        ref = lat.observables()
+        for k in STATE_KEYS:
+            a, r = getattr(ob, k), getattr(ref, k)
+            assert (a == r) or (np.isnan(a) and np.isnan(r)), (rid, k, a, r)
+        assert list(ob.com) == list(ref.com)
+
+
+def test_batch_droplets_converge_and_small_bubbles_collapse():
+    """32^3 droplets of R = 8 converge to a centred droplet; bubbles that small dissolve
+    into the liquid, which the runs must report as COLLAPSED (status bit 1)."""
+    from oracle import eos as E
+    coex = {G: E.coexistence(E.EOS("one_minus_exp"), G)[:2] for G in (-5.0, -5.5, -6.0)}
+    b = P.Batch(3, (32, 32, 32), prec="f32")
+    # Sec. IV: start from the flat-interface coexistence densities of each G
+    drops = [b.enqueue((32, 32, 32), G=G, R=8.0, rho_in=coex[G][1], rho_out=coex[G][0]) for G in coex]
+    bubbles = {G: b.enqueue((32, 32, 32), G=G, R=8.0, rho_in=coex[G][0], rho_out=coex[G][1])
+               for G in (-5.0, -5.5)}
+    lu = b.run(max_steps=30_000, check_every=2048)
+    assert lu > 0
+    for rid in drops:
+        st, ob = b.result(rid)
+        assert st == 0 and ob.criterion in (1, 2), (rid, st, ob.criterion, ob.steps)
+        assert not (ob.status_bits & (2 | 4 | 8 | 16)), ob.status_bits
+        assert ob.dP > 0
+    for G, rid in bubbles.items():
+        st, ob = b.result(rid)
+        assert st in (0, P._lib.LBM_ENOTCONV), st
+        collapsed = abs(ob.n_in - ob.n_out) < 1e-2 * (coex[G][1] - coex[G][0])
+        assert bool(ob.status_bits & 2) == collapsed
+
+
+def test_batch_rejects_boxes_larger_than_its_slots():
+    b = P.Batch(1, (16, 16, 16), prec="f32")
+    with pytest.raises(P.LBMError):
+        b.enqueue((17, 16, 16))
