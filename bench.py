@@ -191,6 +191,33 @@ def cpu_baseline_sample(seconds_target=12.0):
             "sample": f"{n} LB steps of the 128^3 droplet lattice, numpy FP64, single thread"}
 
 
+SWEEP_RADII = (18.0, 20.0, 22.0, 24.0)
+
+
+def sweep_leg():
+    """The sweep of Sec. IV in miniature: G = -5, droplets and bubbles of R in
+    {18, 20, 22, 24} at L = 4R, from the GPU flat-interface coexistence to the Tolman
+    fit; batched shifted-FP32 storage against one-lattice-at-a-time FP64, wall time
+    of each (set-up, runs to convergence and observables included)."""
+    from paper_2105_08772_gb300 import sweep as S
+    runs = S.plan(couplings=(G,), radii=SWEEP_RADII, L_min=0, per_R=4.0)
+    t0 = time.perf_counter()
+    coex = S.coexistence((G,))
+    t_flat = time.perf_counter() - t0
+    ob, wall_b, lu_b = S.run_batched(runs, coex, slots=len(runs), prec="f32", max_steps=30_000)
+    op, wall_p, lu_p = S.run_plain(runs, coex, prec="f64", max_steps=30_000)
+    fb, fp = S.tolman(ob, coex), S.tolman(op, coex)
+    fit = S.compare(fb, fp).get(G)
+    return {"workload": f"G={G}, psi=1-exp(-n), droplets+bubbles R in {list(SWEEP_RADII)}, L=4R",
+            "runs": len(runs), "usable_f32": sum(o.usable for o in ob),
+            "usable_f64": sum(o.usable for o in op), "flat_interface_s": t_flat,
+            "batched_f32_s": wall_b, "plain_f64_s": wall_p, "speedup": wall_p / wall_b,
+            "batched_f32_MLUPS": lu_b / wall_b / 1e6, "plain_f64_MLUPS": lu_p / wall_p / 1e6,
+            "delta_f64": fp[G].delta if G in fp else None,
+            "sigma0_f64": fp[G].sigma0 if G in fp else None,
+            "rel_diff": {**(fit or {}), **{k: v for k, v in S.compare_runs(ob, op).items() if k != "runs"}}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,6 +228,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-sweep-leg", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -322,6 +350,10 @@ def main():
                 "sample": "one 2048-step interval of the 128^3 droplet, FP64 storage and arithmetic",
                 "hbm_gbs": BYTES_PER_LU["f64"] * N * LBM_STEPS_PER_STEP / (ms * 1e-3) / 1e9}
 
+    sweep = None
+    if not args.no_sweep_leg and ws == 1:
+        sweep = sweep_leg()
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -347,6 +379,7 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
         "fp64": fp64,
+        "sweep": sweep,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

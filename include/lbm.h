@@ -234,7 +234,8 @@ const char* lbm_last_error(const lbm_ctx* ctx);
 /* ---------------------------------------------------------------- flat interface */
 
 /* Flat-interface coexistence (Sec. IV, flat-interface paragraph): a strip of gas of
- * width Lx/2 in liquid (Eq. (24), densities rho_g0 / rho_l0) on a periodic
+ * width Lx/2 in liquid (Eq. (24), densities rho_g0 / rho_l0; both 0 = start from
+ * lbm_coexistence_estimate) on a periodic
  * Lx x m x m box (m = 3 for E4, 5 for E6/E8; a field uniform in y and z is the
  * paper's 2-D strip reduced exactly), run until delta u < tol_du (checked every
  * 2^11 steps) or max_steps.  Returns the bulk densities n_g (strip centre) and n_l
@@ -243,6 +244,17 @@ const char* lbm_last_error(const lbm_ctx* ctx);
  * holds lbm_flat_workspace_bytes bytes.  Synchronises; LBM_ENOTCONV still fills
  * the outputs. */
 size_t lbm_flat_workspace_bytes(int Lx, int stencil, int prec);
+
+/* Continuum estimate of the flat-interface coexistence (host only, no device
+ * work): with P_N constant through a flat interface, the continuum limit of the
+ * lattice pressure tensor (Eq. (9)) gives P(n_g) = P(n_l) = p_0 for the bulk
+ * pressure of Eq. (10) and int_{n_g}^{n_l} (p_0 - P(n)) psi'(n)/psi(n) dn = 0.
+ * Solved by bisection on n_g between the spinodals with Gauss-Legendre
+ * quadrature in log n.  The lattice values (lbm_flat_interface) differ from it by
+ * the higher-order terms of Eq. (9), ~1e-3 relative.  LBM_EINVAL when P(n) has
+ * no van der Waals loop (G at or above G_c) or when the condition has no root
+ * (its gas density reaches 0: psi = 1 - exp(-n) below G ~ -6.35).  p0 may be null. */
+lbm_status lbm_coexistence_estimate(lbm_eos eos, double G, double* n_g, double* n_l, double* p0);
 lbm_status lbm_flat_interface(double tau, double G, lbm_eos eos, int stencil, int prec, int Lx,
                               double rho_l0, double rho_g0, long long max_steps, double tol_du,
                               void* dev_workspace, size_t bytes, void* cuda_stream, double* n_g,

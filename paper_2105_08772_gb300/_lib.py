@@ -31,7 +31,7 @@ EXPORTS = (
     "lbm_storage_params", "lbm_density_moments_noalloc", "lbm_batch_workspace_bytes",
     "lbm_batch_create", "lbm_batch_enqueue", "lbm_batch_run", "lbm_batch_result",
     "lbm_batch_last_error", "lbm_batch_destroy", "lbm_pn_profile", "lbm_flat_workspace_bytes",
-    "lbm_flat_interface",
+    "lbm_flat_interface", "lbm_coexistence_estimate",
     "lbm_strerror", "lbm_last_error", "lbm_tolman_fit",
 )
 
@@ -109,6 +109,7 @@ def _load():
         "lbm_batch_destroy": (None, [_P]),
         "lbm_pn_profile": (C.c_int, [_P, _D, C.c_longlong]),
         "lbm_flat_workspace_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
+        "lbm_coexistence_estimate": (C.c_int, [lbm_eos, C.c_double, _D, _D, _D]),
         "lbm_flat_interface": (C.c_int, [C.c_double, C.c_double, lbm_eos, C.c_int, C.c_int, C.c_int,
                                          C.c_double, C.c_double, C.c_longlong, C.c_double, _P,
                                          C.c_size_t, _P, _D, _D, _D, C.POINTER(C.c_longlong)]),

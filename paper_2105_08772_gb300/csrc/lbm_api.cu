@@ -667,6 +667,10 @@ lbm_status lbm_flat_interface(double tau, double G, lbm_eos eos, int stencil, in
   if (!n_g || !n_l || !sigma0) return fail(nullptr, LBM_EINVAL, "null output pointer");
   if (!valid_stencil(stencil)) return fail(nullptr, LBM_EINVAL, "stencil must be 4, 6 or 8");
   if (Lx < 8) return fail(nullptr, LBM_EINVAL, "Lx must be >= 8");
+  if (rho_l0 == 0.0 && rho_g0 == 0.0) {   // start from the continuum coexistence
+    const lbm_status e = lbm_coexistence_estimate(eos, G, &rho_g0, &rho_l0, nullptr);
+    if (e != LBM_OK) return e;
+  }
   if (!(rho_l0 > rho_g0) || !(rho_g0 > 0)) return fail(nullptr, LBM_EINVAL, "need rho_l0 > rho_g0 > 0");
   const int m = 2 * radius_of(stencil) + 1;
   const lbm_box box{Lx, m, m};
@@ -896,6 +900,141 @@ const char* lbm_strerror(lbm_status s) {
 }
 
 const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : g_err; }
+
+// ---------------------------------------------------------------- continuum coexistence
+// Bulk pressure of Eq. (10), P(n) = n c_s^2 + G c_s^2 psi(n)^2 / 2 (e_2 = 1), and
+// the weight psi'(n) / psi(n) of the flat interface's mechanical-stability
+// condition.  To leading order in gradients Eq. (9) gives, through a flat
+// interface, P_N = P(n) + (G c_s^2 / 4) psi psi_xx; with P_N = p_0 constant,
+// (p_0 - P) psi_x / psi = (G c_s^2 / 8) d(psi_x^2)/dx integrates to zero across
+// the interface: int_{n_g}^{n_l} (p_0 - P(n)) psi'/psi dn = 0 with
+// P(n_g) = P(n_l) = p_0 (an equal-area rule in the variable ln psi).
+
+namespace {
+
+struct HostEos {
+  lbm_eos e;
+  double G;
+  double psi(double n) const {
+    if (e.kind == LBM_PSI_EXP_INV) return exp(-1.0 / n);
+    if (e.kind == LBM_PSI_ONE_MINUS_EXP) return -expm1(-n);
+    return sqrt(2.0 * (p_cs(n) - n / 3.0) / (G / 3.0));
+  }
+  double p_cs(double n) const {   // Carnahan-Starling pressure
+    const double q = 0.25 * e.b * n, om = 1.0 - q;
+    return n * e.Rgas * e.T * (1.0 + q + q * q - q * q * q) / (om * om * om) - e.a * n * n;
+  }
+  double dp_cs(double n) const {  // d p_CS / dn
+    const double q = 0.25 * e.b * n, om = 1.0 - q;
+    return e.Rgas * e.T * (1.0 + 4.0 * q + 4.0 * q * q - 4.0 * q * q * q + q * q * q * q) /
+               (om * om * om * om) - 2.0 * e.a * n;
+  }
+  double P(double n) const {
+    if (e.kind == LBM_PSI_CS) return p_cs(n);   // the mapped psi returns p_CS exactly
+    const double p = psi(n);
+    return n / 3.0 + G / 6.0 * p * p;
+  }
+  double dP(double n) const {     // dP/dn = c_s^2 + G c_s^2 psi psi'
+    if (e.kind == LBM_PSI_CS) return dp_cs(n);
+    return 1.0 / 3.0 + G / 3.0 * psi(n) * dpsi(n);
+  }
+  double dpsi(double n) const {
+    if (e.kind == LBM_PSI_EXP_INV) return exp(-1.0 / n) / (n * n);
+    if (e.kind == LBM_PSI_ONE_MINUS_EXP) return exp(-n);
+    return (dp_cs(n) - 1.0 / 3.0) / (G / 3.0 * psi(n));   // from psi^2 = 2 (p_CS - n/3)/(G/3)
+  }
+  double weight(double n) const { return dpsi(n) / psi(n); }
+};
+
+// root of P(n) = p on [a, b] where P is monotone, by bisection
+double bisect_P(const HostEos& h, double p, double a, double b) {
+  double fa = h.P(a) - p;
+  for (int it = 0; it < 200 && b - a > 1e-15 * fabs(b); ++it) {
+    const double m = 0.5 * (a + b), fm = h.P(m) - p;
+    if ((fm < 0) == (fa < 0)) { a = m; fa = fm; } else { b = m; }
+  }
+  return 0.5 * (a + b);
+}
+
+// int_{ng}^{nl} (p0 - P(n)) psi'/psi dn: 5-point Gauss-Legendre on panels
+// uniform in log n (the weight grows like 1/n as n -> 0 for psi = 1 - exp(-n))
+double area(const HostEos& h, double p0, double ng, double nl) {
+  static const double x[5] = {-0.9061798459386640, -0.5384693101056831, 0.0, 0.5384693101056831,
+                              0.9061798459386640};
+  static const double w[5] = {0.2369268850561891, 0.4786286704993665, 0.5688888888888889,
+                              0.4786286704993665, 0.2369268850561891};
+  const int panels = 768;
+  const double a = log(ng), b = log(nl), hw = 0.5 * (b - a) / panels;
+  double s = 0.0;
+  for (int k = 0; k < panels; ++k) {
+    const double mid = a + (2 * k + 1) * hw;
+    for (int j = 0; j < 5; ++j) {
+      const double n = exp(mid + hw * x[j]);
+      s += w[j] * (p0 - h.P(n)) * h.weight(n) * n;
+    }
+  }
+  return s * hw;
+}
+
+}  // namespace
+
+lbm_status lbm_coexistence_estimate(lbm_eos eos, double G, double* n_g, double* n_l, double* p0) {
+  if (!n_g || !n_l) return fail(nullptr, LBM_EINVAL, "null output pointer");
+  if (!isfinite(G) || !(G < 0)) return fail(nullptr, LBM_EINVAL, "G must be negative");
+  if (eos.kind != LBM_PSI_EXP_INV && eos.kind != LBM_PSI_ONE_MINUS_EXP && eos.kind != LBM_PSI_CS)
+    return fail(nullptr, LBM_EINVAL, "unknown psi kind %d", eos.kind);
+  if (eos.kind == LBM_PSI_CS && (!(eos.b > 0) || !(eos.T > 0) || !(eos.a > 0) || !(eos.Rgas > 0)))
+    return fail(nullptr, LBM_EINVAL, "Carnahan-Starling psi needs a, b, Rgas, T > 0");
+  const HostEos h{eos, G};
+  const double lo = eos.kind == LBM_PSI_EXP_INV ? 0.02 : 1e-6;
+  double hi = 4.0;
+  if (eos.kind == LBM_PSI_CS) {
+    // the mapped psi is real while p_CS(n) <= n c_s^2 (G < 0); stay below that density
+    hi = 0.999 * 4.0 / eos.b;
+    for (int k = 1; k <= 20000; ++k) {
+      const double n = lo + (hi - lo) * k / 20000;
+      if (h.p_cs(n) - n / 3.0 >= 0) { hi = lo + (hi - lo) * (k - 1) / 20000; break; }
+    }
+  }
+  // spinodals: the first maximum of P (gas side) and the minimum after it (liquid side)
+  const int M = 20000;
+  double n_sg = -1, n_sl = -1;
+  double prev = h.dP(lo);
+  for (int k = 1; k <= M; ++k) {
+    const double n = lo + (hi - lo) * k / M, d = h.dP(n);
+    if (!isfinite(d)) continue;
+    if (n_sg < 0 && prev > 0 && d <= 0) n_sg = n;
+    else if (n_sg > 0 && prev < 0 && d >= 0) { n_sl = n; break; }
+    prev = d;
+  }
+  if (n_sg < 0 || n_sl < 0)
+    return fail(nullptr, LBM_EINVAL, "P(n) has no van der Waals loop in [%g, %g]: no coexistence", lo, hi);
+  // bisection on n_g in (n_min, n_sg): p_0 = P(n_g), n_l the liquid root above n_sl
+  const double p_floor = fmax(h.P(n_sl), h.P(lo));
+  if (!(h.P(hi) > h.P(n_sg)))
+    return fail(nullptr, LBM_EINVAL, "the liquid branch does not reach the gas spinodal pressure below n = %g", hi);
+  double a = h.P(lo) >= p_floor ? lo : bisect_P(h, p_floor, lo, n_sg);
+  double b = n_sg;
+  a += 1e-12 * (b - a);
+  b -= 1e-12 * (b - a);
+  auto A = [&](double ng) {
+    const double p = h.P(ng);
+    return area(h, p, ng, bisect_P(h, p, n_sl, hi));
+  };
+  double fa = A(a);
+  const double fb = A(b);
+  if ((fa < 0) == (fb < 0))
+    return fail(nullptr, LBM_EINVAL, "the equal-area condition has no root between the spinodals");
+  for (int it = 0; it < 100 && b - a > 1e-15 * b; ++it) {
+    const double m = 0.5 * (a + b), fm = A(m);
+    if ((fm < 0) == (fa < 0)) { a = m; fa = fm; } else { b = m; }
+  }
+  const double ng = 0.5 * (a + b), p = h.P(ng);
+  *n_g = ng;
+  *n_l = bisect_P(h, p, n_sl, hi);
+  if (p0) *p0 = p;
+  return LBM_OK;
+}
 
 lbm_status lbm_tolman_fit(const double* R_s, const double* sigma_s, const int* is_bubble,
                           long long m, int quadratic, double* sigma0, double* delta, double* cc) {

@@ -196,6 +196,17 @@ def lbm_flat_interface(tau, G, eos, stencil, prec, Lx, rho_l0, rho_g0, max_steps
     return st, ng.value, nl.value, s0.value, steps.value
 
 
+def lbm_coexistence_estimate(eos, G) -> tuple[float, float, float]:
+    """(n_g, n_l, p_0) of the continuum flat-interface construction (host only)."""
+    ng, nl, p0 = C.c_double(), C.c_double(), C.c_double()
+    check(_lib_.lbm_coexistence_estimate(eos, float(G), C.byref(ng), C.byref(nl), C.byref(p0)), None)
+    return ng.value, nl.value, p0.value
+
+
+def coexistence_estimate(G, psi="one_minus_exp", cs_T=0.0, a=1.0, b=4.0, Rgas=1.0):
+    return lbm_coexistence_estimate(make_eos(psi, a=a, b=b, Rgas=Rgas, T=cs_T), G)
+
+
 def flat_interface(G, psi="one_minus_exp", stencil="E4", prec="f64", tau=1.0, Lx=100, rho_l0=None,
                    rho_g0=None, max_steps=400_000, tol_du=1e-13, cs_T=0.0):
     """Flat-interface coexistence on the GPU with a torch-owned workspace.
@@ -205,8 +216,9 @@ def flat_interface(G, psi="one_minus_exp", stencil="E4", prec="f64", tau=1.0, Lx
     nbytes = lbm_flat_workspace_bytes(Lx, st_, pr)
     ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
     ptr = ws.data_ptr() + (-ws.data_ptr()) % 256
-    rl = 2.0 if rho_l0 is None else rho_l0
-    rg = 0.15 if rho_g0 is None else rho_g0
+    # both 0: the library starts from its continuum coexistence estimate
+    rl = 0.0 if rho_l0 is None else rho_l0
+    rg = 0.0 if rho_g0 is None else rho_g0
     return lbm_flat_interface(tau, G, make_eos(psi, T=cs_T), st_, pr, Lx, rl, rg, max_steps, tol_du, ptr,
                               nbytes, torch.cuda.current_stream().cuda_stream)
 

@@ -1,0 +1,299 @@
+"""The measurement sweep of Sec. IV: droplets and bubbles over radii and couplings.
+
+For each coupling G the flat interface (Eq. (24), run on the GPU by
+lbm_flat_interface) gives the bulk densities n_g, n_l that initialise the
+droplets and bubbles (Eq. (23): droplets n_in = n_l, bubbles n_in = n_g) and the
+flat tension sigma_0 of Eq. (25).  Every droplet and bubble then runs to
+hydrostatic equilibrium under the two convergence tests of Sec. IV, and its
+observables (R_e, Delta P, sigma[R], R_s, sigma_s = Delta P R_s / 2) feed
+
+* the Tolman fit of Eq. (22): sigma_s = sigma_0 (1 - 2 delta x + c x^2) with
+  x = +1/R_s for droplets and -1/R_s for bubbles (lbm_tolman_fit), and
+* the alternative Tolman length of Sec. IV (last paragraph),
+  hat-delta_+- = +-(R_e - R_s), extrapolated to the flat limit 1/R_s -> 0 by a
+  straight line in the signed curvature x.
+
+Two ways to run the same list of problems:
+* run_batched: every lattice in a lbm_batch (uneven boxes advance together, one
+  launch per time step, graph-captured, slots refilled as lattices finish);
+* run_plain: one lattice at a time through lbm_create / lbm_run_to_convergence.
+
+Everything runs on the GPU through liblbm.so; this module only plans the runs,
+calls the library and collects the results.
+
+Command line:  python -m paper_2105_08772_gb300.sweep --couplings -5.0 --radii 6:40:2
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+from dataclasses import asdict, dataclass, field
+
+import numpy as np
+
+from . import _lib
+from .lbm import Batch, Lattice, flat_interface, lbm_tolman_fit
+
+RADII = tuple(range(6, 41, 2))
+COUPLINGS = (-4.6, -5.0, -5.5, -6.0)
+
+# lbm_obs.status_bits that disqualify a run from the fits
+_BAD_BITS = 1 | 2 | 4 | 8 | 16     # no sigma minimum, collapsed, off centre, non-finite, timeout
+
+
+def box_side(R: float, L_min: int = 64, per_R: float = 4.0, L_max: int | None = None) -> int:
+    """Side of the periodic box of a run of initial radius R: max(L_min, ceil(per_R R))."""
+    L = max(int(L_min), int(math.ceil(per_R * R - 1e-9)))
+    if L_max is not None and L > L_max:
+        raise ValueError(f"R = {R} needs a box of {L} > {L_max}")
+    return L
+
+
+@dataclass(frozen=True)
+class Run:
+    G: float
+    bubble: bool
+    R: float
+    L: int
+    psi: str = "one_minus_exp"
+    tau: float = 1.0
+
+
+@dataclass
+class Outcome:
+    run: Run
+    status: int
+    obs: dict = field(default_factory=dict)
+
+    @property
+    def usable(self) -> bool:
+        """Converged, centred, with a minimum of sigma[R] (Sec. IV's analysis condition)."""
+        return (self.status == _lib.LBM_OK and not (int(self.obs.get("status_bits", 0)) & _BAD_BITS)
+                and self.obs.get("R_s", 0.0) > 0.0)
+
+    @property
+    def x(self) -> float:
+        """Signed curvature: +1/R_s for droplets, -1/R_s for bubbles (Sec. IV)."""
+        return (-1.0 if self.run.bubble else 1.0) / self.obs["R_s"]
+
+    @property
+    def delta_hat(self) -> float:
+        """hat-delta_+- = +-(R_e - R_s), + for droplets, - for bubbles (Sec. IV)."""
+        d = self.obs["R_e"] - self.obs["R_s"]
+        return -d if self.run.bubble else d
+
+
+def plan(couplings=COUPLINGS, radii=RADII, psi: str = "one_minus_exp", kinds=("drop", "bubble"),
+         L_min: int = 64, per_R: float = 4.0, tau: float = 1.0) -> list[Run]:
+    """All (G, kind, R) problems, largest box first (the longest runs start first)."""
+    runs = [Run(float(G), k == "bubble", float(R), box_side(R, L_min, per_R), psi, tau)
+            for G in couplings for k in kinds for R in radii]
+    runs.sort(key=lambda r: (-r.L, r.G, r.bubble, r.R))
+    return runs
+
+
+def coexistence(couplings, psi: str = "one_minus_exp", stencil: str = "E4", Lx: int = 100,
+                tol_du: float = 1e-13, max_steps: int = 400_000) -> dict:
+    """Flat-interface bulk densities and sigma_0 per coupling, FP64 on the GPU, each
+    started from the library's continuum estimate.
+    G -> {"n_g", "n_l", "sigma0", "steps", "status"}."""
+    out = {}
+    for G in couplings:
+        st, ng, nl, s0, steps = flat_interface(G, psi=psi, stencil=stencil, prec="f64", Lx=Lx,
+                                               max_steps=max_steps, tol_du=tol_du)
+        out[float(G)] = {"n_g": ng, "n_l": nl, "sigma0": s0, "steps": steps, "status": st}
+    return out
+
+
+def _densities(run: Run, coex: dict) -> tuple[float, float]:
+    c = coex[run.G]
+    return (c["n_g"], c["n_l"]) if run.bubble else (c["n_l"], c["n_g"])
+
+
+def _sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def run_batched(runs, coex, slots: int = 64, prec: str = "f32", stencil: str = "E4",
+                max_steps: int = 50_000, check_every: int = 2048, tol_dP_rel: float = 1e-5,
+                tol_du: float = 1e-12, width: float = 1.0):
+    """All runs through one lbm_batch.  Returns (outcomes, wall seconds, lattice updates)."""
+    L = max(r.L for r in runs)
+    _sync()
+    t0 = time.perf_counter()
+    b = Batch(min(slots, len(runs)), (L, L, L), stencil=stencil, prec=prec)
+    try:
+        ids = []
+        for r in runs:
+            n_in, n_out = _densities(r, coex)
+            ids.append(b.enqueue((r.L, r.L, r.L), tau=r.tau, G=r.G, psi=r.psi, R=r.R, rho_in=n_in,
+                                 rho_out=n_out, width=width))
+        lu = b.run(max_steps=max_steps, check_every=check_every, tol_dP_rel=tol_dP_rel, tol_du=tol_du)
+        outs = []
+        for r, rid in zip(runs, ids):
+            st, o = b.result(rid)
+            outs.append(Outcome(r, st, o.as_dict()))
+    finally:
+        b.close()
+    _sync()
+    return outs, time.perf_counter() - t0, lu
+
+
+def run_plain(runs, coex, prec: str = "f64", stencil: str = "E4", max_steps: int = 50_000,
+              check_every: int = 2048, tol_dP_rel: float = 1e-5, tol_du: float = 1e-12,
+              width: float = 1.0):
+    """One lattice at a time.  Returns (outcomes, wall seconds, lattice updates)."""
+    _sync()
+    t0 = time.perf_counter()
+    outs, lu = [], 0
+    for r in runs:
+        lat = Lattice(r.L, r.L, r.L, tau=r.tau, G=r.G, psi=r.psi, stencil=stencil, prec=prec)
+        try:
+            n_in, n_out = _densities(r, coex)
+            c = r.L // 2
+            lat.init_drop((c, c, c), r.R, n_in, n_out, width)
+            crit = 0
+            try:
+                st, _, crit = lat.run_to_convergence(max_steps=max_steps, check_every=check_every,
+                                                     tol_dP_rel=tol_dP_rel, tol_du=tol_du)
+            except _lib.LBMError as e:
+                st = e.status
+            # the observables of the field the run ended on (recomputed, same values)
+            o = lat.observables().as_dict()
+            o["criterion"] = crit
+            lu += int(o["steps"]) * lat.N
+            outs.append(Outcome(r, st, o))
+        finally:
+            lat.close()
+    _sync()
+    return outs, time.perf_counter() - t0, lu
+
+
+@dataclass
+class TolmanResult:
+    G: float
+    sigma0: float          # extrapolated flat tension (Eq. (22) at x = 0)
+    delta: float           # Tolman length
+    c: float               # second-order coefficient
+    delta_hat0: float      # hat-delta extrapolated to 1/R_s -> 0
+    n_used: int
+    sigma0_lin: float = 0.0    # the same fit without the x^2 term (Sec. IV's straight lines)
+    delta_lin: float = 0.0
+    sigma0_flat: float | None = None
+
+
+def tolman(outcomes, coex: dict | None = None, quadratic: bool = True, min_runs: int = 4) -> dict:
+    """Per coupling: the fit of Eq. (22) over the usable runs, and the flat-limit
+    hat-delta (straight line in x).  G -> TolmanResult."""
+    res = {}
+    for G in sorted({o.run.G for o in outcomes}):
+        use = [o for o in outcomes if o.run.G == G and o.usable]
+        if len(use) < min_runs:
+            continue
+        Rs = np.array([o.obs["R_s"] for o in use])
+        ss = np.array([o.obs["sigma_s"] for o in use])
+        bub = np.array([o.run.bubble for o in use], dtype=np.int32)
+        s0, d, c = lbm_tolman_fit(Rs, ss, bub, quadratic=quadratic)
+        s0l, dl, _ = lbm_tolman_fit(Rs, ss, bub, quadratic=False)
+        x = np.array([o.x for o in use])
+        dh = np.array([o.delta_hat for o in use])
+        A = np.stack([np.ones_like(x), x], axis=1)
+        dh0 = float(np.linalg.lstsq(A, dh, rcond=None)[0][0])
+        res[G] = TolmanResult(G, s0, d, c, dh0, len(use), s0l, dl,
+                              None if coex is None else coex[G]["sigma0"])
+    return res
+
+
+def compare(a: dict, b: dict) -> dict:
+    """Relative differences of sigma_0 and delta (and hat-delta_0) between two fits."""
+    out = {}
+    for G in sorted(set(a) & set(b)):
+        ra, rb = a[G], b[G]
+        out[G] = {"sigma0": abs(ra.sigma0 - rb.sigma0) / abs(rb.sigma0),
+                  "delta": abs(ra.delta - rb.delta) / abs(rb.delta),
+                  "delta_hat0": abs(ra.delta_hat0 - rb.delta_hat0) / abs(rb.delta_hat0)}
+    return out
+
+
+def compare_runs(a, b) -> dict:
+    """Largest relative difference of R_s and sigma_s over runs usable in both lists."""
+    key = lambda o: (o.run.G, o.run.bubble, o.run.R)  # noqa: E731
+    bm = {key(o): o for o in b}
+    dRs = dss = 0.0
+    n = 0
+    for o in a:
+        p = bm.get(key(o))
+        if p is None or not (o.usable and p.usable):
+            continue
+        n += 1
+        dRs = max(dRs, abs(o.obs["R_s"] - p.obs["R_s"]) / p.obs["R_s"])
+        dss = max(dss, abs(o.obs["sigma_s"] - p.obs["sigma_s"]) / p.obs["sigma_s"])
+    return {"runs": n, "R_s": dRs, "sigma_s": dss}
+
+
+def _parse_radii(s: str):
+    if ":" in s:
+        a, b, c = (float(v) for v in s.split(":"))
+        return tuple(np.arange(a, b + 0.5 * c, c))
+    return tuple(float(v) for v in s.split(","))
+
+
+def main(argv=None) -> dict:
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--couplings", default=",".join(str(g) for g in COUPLINGS))
+    ap.add_argument("--radii", default="6:40:2")
+    ap.add_argument("--psi", default="one_minus_exp")
+    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--prec", default="f32")
+    ap.add_argument("--max-steps", type=int, default=50_000)
+    ap.add_argument("--L-min", type=int, default=64)
+    ap.add_argument("--per-R", type=float, default=4.0)
+    ap.add_argument("--plain", default="", help="couplings also run one lattice at a time in FP64")
+    ap.add_argument("--out", default="")
+    a = ap.parse_args(argv)
+    couplings = tuple(float(g) for g in a.couplings.split(","))
+    radii = _parse_radii(a.radii)
+    runs = plan(couplings, radii, psi=a.psi, L_min=a.L_min, per_R=a.per_R)
+    t0 = time.perf_counter()
+    coex = coexistence(couplings, psi=a.psi)
+    t_flat = time.perf_counter() - t0
+    outs, wall, lu = run_batched(runs, coex, slots=a.slots, prec=a.prec, max_steps=a.max_steps)
+    fit = tolman(outs, coex)
+    report = {"runs": len(runs), "usable": sum(o.usable for o in outs), "flat_wall_s": t_flat,
+              "batched": {"prec": a.prec, "slots": a.slots, "wall_s": wall, "lattice_updates": lu,
+                          "MLUPS": lu / wall / 1e6},
+              "coexistence": {str(G): v for G, v in coex.items()},
+              "fit": {str(G): asdict(r) for G, r in fit.items()}}
+    if a.plain:
+        pc = tuple(float(g) for g in a.plain.split(","))
+        sub = [r for r in runs if r.G in pc]
+        sub_b = [o for o in outs if o.run.G in pc]
+        outs_p, wall_p, lu_p = run_plain(sub, coex, prec="f64", max_steps=a.max_steps)
+        fit_p = tolman(outs_p, coex)
+        # the batched path on the same subset alone, for a like-for-like wall time
+        outs_s, wall_s, lu_s = run_batched(sub, coex, slots=a.slots, prec=a.prec, max_steps=a.max_steps)
+        report["plain_f64"] = {"runs": len(sub), "wall_s": wall_p, "lattice_updates": lu_p,
+                               "MLUPS": lu_p / wall_p / 1e6,
+                               "fit": {str(G): asdict(r) for G, r in fit_p.items()}}
+        report["batched_subset"] = {"runs": len(sub), "wall_s": wall_s, "lattice_updates": lu_s,
+                                    "MLUPS": lu_s / wall_s / 1e6}
+        report["batched_vs_plain"] = {"fit": {str(G): v for G, v in compare(fit, fit_p).items()},
+                                      "runs": compare_runs(sub_b, outs_p)}
+    report["per_run"] = [{"G": o.run.G, "bubble": o.run.bubble, "R": o.run.R, "L": o.run.L,
+                          "status": o.status, "usable": o.usable,
+                          **{k: o.obs[k] for k in ("R_e", "R_s", "sigma_s", "dP", "n_in", "n_out",
+                                                   "steps", "status_bits", "criterion")}}
+                         for o in outs]
+    text = json.dumps(report, indent=1)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(text)
+    print(json.dumps({k: v for k, v in report.items() if k != "per_run"}, indent=1))
+    return report
+
+
+if __name__ == "__main__":
+    main()

@@ -121,3 +121,26 @@ def test_tolman_fit_skips_points_without_a_minimum():
     assert abs(s0 - s0r) < 1e-14 and abs(d - dr) < 1e-12
     with pytest.raises(P.LBMError):
         P.lbm_tolman_fit(Rs[:1], sig[:1], np.zeros(1, dtype=np.int32), quadratic=False)
+
+
+@pytest.mark.parametrize("kind,G,tfrac", [("one_minus_exp", -4.2, 0), ("one_minus_exp", -5.0, 0),
+                                          ("one_minus_exp", -6.0, 0), ("exp_inv", -np.e ** 2 * 1.1, 0),
+                                          ("exp_inv", -np.e ** 2 * 1.293, 0), ("cs", -1.0, 0.8),
+                                          ("cs", -1.0, 0.9)])
+def test_coexistence_estimate_matches_oracle(kind, G, tfrac):
+    """lbm_coexistence_estimate (bisection on n_g, Gauss-Legendre in log n) against the
+    oracle's construction (bisection on p_0, adaptive quadrature): the same equal-area
+    condition solved two independent ways."""
+    from oracle import eos as E
+    T = tfrac * E.cs_critical_temperature(E.EOS("cs"))[1] if kind == "cs" else 0.0
+    ng, nl, p0 = P.coexistence_estimate(G, psi=kind, cs_T=T)
+    lo = 0.02 if kind == "exp_inv" else 1e-3
+    rg, rl, rp = E.coexistence(E.EOS(kind, T=T), G, lo=lo, hi=4.0 if kind != "cs" else 1.1 * nl)
+    assert abs(ng - rg) < 1e-11 * rg and abs(nl - rl) < 1e-11 * rl and abs(p0 - rp) < 1e-11 * abs(rp)
+
+
+def test_coexistence_estimate_rejects_no_loop():
+    with pytest.raises(P.LBMError):
+        P.coexistence_estimate(-3.9)             # above G_c = -4: no van der Waals loop
+    with pytest.raises(P.LBMError):
+        P.coexistence_estimate(-7.0)             # the construction's gas density has reached 0

@@ -1,0 +1,56 @@
+"""A small sweep of Sec. IV on the GPU: flat-interface coexistence, droplets and
+bubbles at R = L/4 (the paper's aspect ratio; at G = -5 bubbles below R ~ 18
+dissolve, the liquid being compressible enough to take up their gas), batched
+FP32-shifted storage against one-at-a-time FP64, and the Tolman fit of Eq. (22).
+
+Each lattice of the batch is bitwise the single-lattice run (tests/test_gpu_batch.py)
+and the single-lattice run matches the oracle (tests/test_gpu_parity.py); here the
+question is the end result: does FP32 storage give the FP64 R_s, sigma_s and
+Tolman length, and does the physics have the paper's signs."""
+import pytest
+
+S = pytest.importorskip("paper_2105_08772_gb300.sweep")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sweep():
+    runs = S.plan(couplings=(-5.0,), radii=(18.0, 20.0, 22.0, 24.0), L_min=0, per_R=4.0)
+    coex = S.coexistence((-5.0,))
+    b, wall_b, lu_b = S.run_batched(runs, coex, slots=8, prec="f32", max_steps=30_000)
+    p, wall_p, lu_p = S.run_plain(runs, coex, prec="f64", max_steps=30_000)
+    return runs, coex, b, p
+
+
+def test_every_run_converges_with_a_surface_of_tension(sweep):
+    runs, coex, b, p = sweep
+    assert [r.L for r in runs] == [96, 96, 88, 88, 80, 80, 72, 72]
+    for o in b + p:
+        assert o.usable, (o.run, o.status, o.obs["status_bits"])
+
+
+def test_f32_batched_matches_f64_plain(sweep):
+    """Per run R_s and sigma_s to 2e-4; the fitted sigma_0 and delta to 1e-3."""
+    runs, coex, b, p = sweep
+    d = S.compare_runs(b, p)
+    assert d["runs"] == len(runs)
+    assert d["R_s"] < 2e-4 and d["sigma_s"] < 2e-4, d
+    fb, fp = S.tolman(b, coex), S.tolman(p, coex)
+    r = S.compare(fb, fp)[-5.0]
+    assert r["sigma0"] < 1e-3 and r["delta"] < 1e-3, r
+
+
+def test_curvature_corrections_have_the_papers_signs(sweep):
+    """Sec. IV: droplets (x > 0) sit below sigma_0, bubbles above; delta > 0; the
+    extrapolated sigma_0 is close to the flat interface's (Eq. (25))."""
+    runs, coex, b, p = sweep
+    s0_flat = coex[-5.0]["sigma0"]
+    for o in p:
+        if o.run.bubble:
+            assert o.obs["sigma_s"] > s0_flat
+        else:
+            assert o.obs["sigma_s"] < s0_flat
+    fit = S.tolman(p, coex)[-5.0]
+    assert fit.delta > 0
+    assert abs(fit.sigma0 - s0_flat) < 0.05 * s0_flat
