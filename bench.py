@@ -229,6 +229,7 @@ def main():
     ap.add_argument("--no-fp64-leg", action="store_true")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-sweep-leg", action="store_true")
+    ap.add_argument("--no-large-leg", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -350,6 +351,31 @@ def main():
                 "sample": "one 2048-step interval of the 128^3 droplet, FP64 storage and arithmetic",
                 "hbm_gbs": BYTES_PER_LU["f64"] * N * LBM_STEPS_PER_STEP / (ms * 1e-3) / 1e9}
 
+    # the same step kernel on a 256^3 lattice (4x the 128^3 working set): the
+    # roofline fraction at a size well past L2
+    large = None
+    if not args.no_large_leg and args.prec != "f64":
+        L = 256
+        with torch.cuda.stream(stream):
+            big = P.Lattice(L, L, L, tau=TAU, G=G, psi="one_minus_exp", stencil="E4", prec=args.prec,
+                            stream=stream)
+        big.init_drop((L // 2,) * 3, L / 4, RHO_L, RHO_G)
+        big.step(256)
+        big.observables()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_big = 1024
+        torch.cuda.synchronize()
+        e0.record(stream)
+        big.step(n_big)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / n_big
+        ach = BYTES_PER_LU[args.prec] * L ** 3 / (us * 1e-6) / 1e9
+        large = {"box": L, "avg_launch_us": us, "MLUPS": L ** 3 / us, "achieved": ach, "unit": "GB/s",
+                 "frac": ach / peak, "tile": big.get_tile(),
+                 "sample": f"{n_big} steps of a 256^3 droplet (R=64), same kernel and storage"}
+        big.close()
+
     sweep = None
     if not args.no_sweep_leg and ws == 1:
         sweep = sweep_leg()
@@ -379,6 +405,7 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
         "fp64": fp64,
+        "roofline_256": large,
         "sweep": sweep,
     }
     print(json.dumps(line), flush=True)

@@ -195,8 +195,19 @@ __device__ __forceinline__ void async_process_item(const LatticeDesc& d, int zch
   }
 }
 
+// CTAs per SM a variant is compiled for: as many as its shared memory admits
+// (228 KB per SM, 1 KB reserved per CTA), capped so that no thread is given
+// fewer than 64 registers; __launch_bounds__ then caps the registers at
+// 65536 / (threads x blocks), so registers never limit residency further.
+template <int NT, size_t SMEM>
+constexpr int async_min_blocks() {
+  constexpr int by_smem = (int)((228u * 1024u) / (SMEM + 1024u));
+  constexpr int by_regs = 65536 / (NT * 64);
+  return by_smem < 1 ? 1 : (by_smem > by_regs ? by_regs : by_smem);
+}
+
 template <int P, int ST, int BX, int BY, int D, bool UNIT_TAU>
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(BX * BY, (async_min_blocks<BX * BY, AsyncShape<P, ST, BX, BY, D>::smem_bytes>()))
 lattice_async_kernel(LatticeDesc d, int zchunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ncols = ((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);

@@ -49,12 +49,14 @@ def test_flat_converged_coexistence_matches_oracle(G):
 
 def test_flat_f32_storage_close_to_f64():
     """FP32 storage (shifted populations) run for the steps FP64 needed to reach rest
-    lands on the FP64 coexistence to ~1e-5."""
+    (~4e4) lands on the FP64 coexistence: n_l to 1e-5, n_g to 3e-4 (its FP32 rounding
+    relative to the storage shift n0 ~ 1 is ~8x larger than relative to n_g), sigma_0
+    to 1e-3."""
     st64, ng64, nl64, s64, done = P.flat_interface(-5.0, Lx=100, prec="f64", tol_du=1e-13)
     st32, ng32, nl32, s32, _ = P.flat_interface(-5.0, Lx=100, prec="f32", max_steps=done,
                                                 tol_du=-1.0)
     assert st64 == P.LBM_OK and st32 == P.LBM_ENOTCONV
-    assert abs(ng32 - ng64) < 1e-4 * ng64 and abs(nl32 - nl64) < 1e-5 * nl64, (ng32, ng64, nl32, nl64)
+    assert abs(ng32 - ng64) < 3e-4 * ng64 and abs(nl32 - nl64) < 1e-5 * nl64, (ng32, ng64, nl32, nl64)
     assert abs(s32 - s64) < 1e-3 * s64, (s32, s64)
 
 
