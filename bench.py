@@ -56,7 +56,8 @@ def measured_peak_gbs():
     return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("lbm_common.cuh", "lbm_kernels.cuh", "lbm_kernels_async.cuh", "lbm_lattice_inst.cuh")
+KERNEL_SOURCES = ("lbm_common.cuh", "lbm_kernels.cuh", "lbm_kernels_async.cuh", "lbm_kernels_chunk.cuh",
+                  "lbm_kernels_moment.cuh", "lbm_lattice_inst.cuh")
 
 
 def measured_traffic(prec):
@@ -397,7 +398,8 @@ def main():
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "kernel": "fused step (pull + on-chip psi halo + SC force + Guo-BGK + store)",
+                     "kernel": "fused step, lattice_moment_kernel (pull + on-chip psi halo + SC force "
+                               "+ Guo-BGK at tau = 1 + store)",
                      "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": len(lats) * N * 8,

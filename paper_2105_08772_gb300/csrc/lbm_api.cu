@@ -160,8 +160,25 @@ TileCfg default_tile(lbm_box b, int prec, int stencil) {
   t.bx = 32;
   t.by = stencil == 4 ? 8 : 4;
   if (prec == kF16) return t;   // register-load kernel
-  // pipelined kernel with a launcher-chosen z chunk, if one compiled shape fits
   const int R = stencil == 4 ? 1 : 2;
+  // the moment kernel (tau = 1; the chunked kernel otherwise) when the rows split
+  // into 16-byte chunks: 64 x 4 tiles for FP32 E4 boxes at least 72 wide, else 32 x 8
+  // (E4) or 32 x 4 (wider stencils), provided both kernels fit one CTA
+  if (b.nx % 4 == 0) {
+    const int shapes[2][2] = {{64, 4}, {32, stencil == 4 ? 8 : 4}};
+    for (const auto& sh : shapes) {
+      if (sh[0] == 64 && (stencil != 4 || prec != kF32)) continue;
+      if (b.nx < sh[0] + 8) continue;
+      if (chunk_smem_bytes(prec == kF64 ? 8 : 4, R, sh[0], sh[1], 1) > kMaxSmemPerCta) continue;
+      t.kind = 5;
+      t.bx = sh[0];
+      t.by = sh[1];
+      t.zchunk = 0;
+      t.depth = 1;
+      return t;
+    }
+  }
+  // pipelined kernel with a launcher-chosen z chunk, if one compiled shape fits
   const int by_pref[2] = {(prec == kF64 || stencil != 4) ? 4 : 8, 4};
   for (int by : by_pref) {
     if (async_smem_bytes(prec == kF64 ? 8 : 4, R, 32, by, 1) <= kMaxSmemPerCta) {
@@ -206,6 +223,36 @@ std::vector<TileCfg> step_candidates(const lbm_ctx* c) {
         TileCfg t{bs[k][0], bs[k][1], zc};
         t.kind = 2;
         t.depth = bs[k][2];
+        out.push_back(t);
+      }
+    }
+    const int (*ms)[3] = c->stencil == 4 ? kMomentE4 : kMomentWide;
+    const int nm = c->stencil == 4 ? kNumMomentE4 : kNumMomentWide;
+    for (int k = 0; k < nm; ++k) {
+      // the chunked kernel's requirements; both it and the chunked fallback must fit
+      if (c->box.nx % 4 != 0 || c->box.nx < ms[k][0] + 8) continue;
+      if (chunk_smem_bytes(storage_bytes(c->prec), R, ms[k][0], ms[k][1], ms[k][2]) > kMaxSmemPerCta)
+        continue;
+      for (int zc : {0, 8, 16, 32}) {
+        if (zc > c->box.nz) continue;
+        TileCfg t{ms[k][0], ms[k][1], zc};
+        t.kind = 5;
+        t.depth = ms[k][2];
+        out.push_back(t);
+      }
+    }
+    const int (*cs)[3] = c->stencil == 4 ? kChunkE4 : kChunkWide;
+    const int nc = c->stencil == 4 ? kNumChunkE4 : kNumChunkWide;
+    for (int k = 0; k < nc; ++k) {
+      // 16-byte chunks of whole rows: nx % 4 == 0, and a staged row wraps at most once
+      if (c->box.nx % 4 != 0 || c->box.nx < cs[k][0] + 8) continue;
+      if (chunk_smem_bytes(storage_bytes(c->prec), R, cs[k][0], cs[k][1], cs[k][2]) > kMaxSmemPerCta)
+        continue;
+      for (int zc : {0, 8, 16, 32}) {
+        if (zc > c->box.nz) continue;
+        TileCfg t{cs[k][0], cs[k][1], zc};
+        t.kind = 4;
+        t.depth = cs[k][2];
         out.push_back(t);
       }
     }
@@ -1127,7 +1174,7 @@ struct lbm_batch {
   std::vector<lbm_obs> obs_host;
   cudaGraphExec_t graph = nullptr;
   int graph_len = 0;
-  int graph_unit_tau = -1;
+  int graph_mode = -1;       // BatchMode the graph (and the table's tiling) was made for
   long long lattice_updates = 0;
   char err[512];
 };
@@ -1163,10 +1210,16 @@ BatchLayout batch_layout(int slots, lbm_box max_box, int stencil, int prec) {
   return L;
 }
 
-bool batch_unit_tau(const lbm_batch* b) {
-  for (const BatchRun& r : b->runs)
-    if (r.tau != 1.0) return false;
-  return true;
+// kernel mode of the whole queue: the moment kernel needs tau = 1 and boxes whose
+// rows split into 16-byte chunks (nx % 4 == 0) at least a tile plus apron wide
+int batch_mode(const lbm_batch* b) {
+  bool unit = true, moment = true;
+  const int bx = batch_tile(b->prec, b->stencil, kBatchMoment).bx;
+  for (const BatchRun& r : b->runs) {
+    if (r.tau != 1.0) unit = false;
+    if (r.box.nx % 4 != 0 || r.box.nx < bx + 8) moment = false;
+  }
+  return !unit ? kBatchMixedTau : (moment ? kBatchMoment : kBatchUnitTau);
 }
 
 lbm_status batch_fill(lbm_batch* b) {
@@ -1201,7 +1254,7 @@ lbm_status batch_fill(lbm_batch* b) {
 
 // table of the active lattices, in slot order, with their global work items
 lbm_status batch_upload(lbm_batch* b) {
-  const TileCfg t = batch_tile(b->prec, b->stencil);
+  const TileCfg t = batch_tile(b->prec, b->stencil, b->graph_mode);
   b->table_host.clear();
   long long items = 0;
   for (int k = 0; k < b->slots; ++k) {
@@ -1228,18 +1281,18 @@ lbm_status batch_upload(lbm_batch* b) {
   return LBM_OK;
 }
 
-lbm_status batch_graph(lbm_batch* b, int len, bool unit_tau) {
-  if (b->graph && b->graph_len == len && b->graph_unit_tau == (int)unit_tau) return LBM_OK;
+lbm_status batch_graph(lbm_batch* b, int len, int mode) {
+  if (b->graph && b->graph_len == len && b->graph_mode == mode) return LBM_OK;
   if (b->graph) cudaGraphExecDestroy(b->graph);
   b->graph = nullptr;
   int grid = 0;
-  LBM_BCUDA(b, launch_batch(b->prec, b->stencil, unit_tau, b->table_dev, b->hdr_dev, 0, true, &grid,
+  LBM_BCUDA(b, launch_batch(b->prec, b->stencil, mode, b->table_dev, b->hdr_dev, 0, true, &grid,
                                  b->stream));
   cudaGraph_t g = nullptr;
   LBM_BCUDA(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < len && e == cudaSuccess; ++k)
-    e = launch_batch(b->prec, b->stencil, unit_tau, b->table_dev, b->hdr_dev, k & 1, false, nullptr,
+    e = launch_batch(b->prec, b->stencil, mode, b->table_dev, b->hdr_dev, k & 1, false, nullptr,
                      b->cap_stream);
   cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -1254,7 +1307,7 @@ lbm_status batch_graph(lbm_batch* b, int len, bool unit_tau) {
     return bfail(b, LBM_ECUDA, "batch graph instantiate failed: %s", cudaGetErrorString(e));
   }
   b->graph_len = len;
-  b->graph_unit_tau = unit_tau;
+  b->graph_mode = mode;
   return LBM_OK;
 }
 
@@ -1349,10 +1402,10 @@ lbm_status lbm_batch_run(lbm_batch* b, long long max_steps, long long check_ever
   if (!b) return bfail(nullptr, LBM_EINVAL, "null batch");
   if (max_steps < 0 || check_every < 2) return bfail(b, LBM_EINVAL, "max_steps >= 0, check_every >= 2");
   const int K = (int)(check_every + (check_every & 1));   // even: a graph keeps every parity
-  const bool unit_tau = batch_unit_tau(b);
+  const int mode = batch_mode(b);
   lbm_status st = batch_fill(b);
   if (st != LBM_OK) return st;
-  st = batch_graph(b, K, unit_tau);
+  st = batch_graph(b, K, mode);
   if (st != LBM_OK) return st;
   for (;;) {
     int active = 0;

@@ -1,0 +1,260 @@
+// Unit-relaxation-time variant of the pipelined Shan-Chen step (FP32 / FP64).
+//
+// With tau = 1 the BGK update of Eq. (4) loses its f_i term:
+//     f*_i = f_i - (f_i - f_i^eq) + F_i = f_i^eq(n, u) + F_i,
+// so a node's post-collision populations depend on its own populations only
+// through n and the momentum j = sum_i xi_i f_i (u = (j + F/2)/n, Eq. (7)).
+// The collision of plane z therefore needs, from its stage, just four numbers
+// per node -- and those can be formed in the same pass that forms the density
+// for psi.  The kernel keeps them in registers for the R planes until psi of
+// plane z + R exists, so a population stage is free as soon as its densities
+// are formed: NS = 1 + D stages instead of R + 1 + D.  The smaller footprint
+// fits more CTAs per SM.
+//
+// Copies: the 16-byte row chunks of the chunked kernel (lbm_kernels_chunk.cuh).
+// Thread roles in the density pass: each thread forms its own column's padded
+// node (ty + R, tx + R) -- its interior node, whose moments it keeps -- and
+// the NPAD - NT nodes of the halo ring are dealt out to the threads.
+// The arithmetic per node is the chunked kernel's (same sums, same collide), so
+// fields are bitwise equal to it.
+#pragma once
+
+#include "lbm_kernels_chunk.cuh"
+
+namespace lbm {
+
+template <int P, int ST, int BX, int BY, int D>
+struct MomentShape {
+  using T = typename Storage<P>::T;
+  static constexpr int R = stencil_radius<ST>();
+  static constexpr int PX = BX + 2 * R;
+  static constexpr int PY = BY + 2 * R;
+  static constexpr int NPAD = PX * PY;
+  static constexpr int NT = BX * BY;
+  static constexpr int NH = NPAD - NT;                 // halo ring nodes
+  static constexpr int NHPER = (NH + NT - 1) / NT;     // halo nodes per thread
+  static constexpr int XW = BX + 2 * kBulkApron;
+  static constexpr int VE = 16 / (int)sizeof(T);
+  static constexpr int NCH = XW / VE;
+  static constexpr int NS = 1 + D;
+  static constexpr int NR = 2 * R + 1;
+  static constexpr size_t stage_elems = (size_t)Q * PY * XW;
+  static constexpr size_t smem_bytes = sizeof(T) * (NS * stage_elems + NR * NPAD);
+  static_assert(R + 1 <= kBulkApron, "apron must cover the pull of the halo");
+};
+
+// padded index of the h-th node of the halo ring: R full rows on top, R on the
+// bottom, then R columns on each side of the BY middle rows
+template <int R, int PX, int PY>
+__device__ __forceinline__ int halo_node(int h) {
+  if (h < R * PX) return h;
+  h -= R * PX;
+  if (h < R * PX) return (PY - R) * PX + h;
+  h -= R * PX;
+  const int row = R + h / (2 * R), c = h % (2 * R);
+  return row * PX + (c < R ? c : PX - 2 * R + c);
+}
+
+template <int P, int ST, int BX, int BY, int D>
+__device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zchunk, long long item,
+                                                    unsigned char* smem_raw) {
+  using Sh = MomentShape<P, ST, BX, BY, D>;
+  using T = typename Sh::T;
+  using S = typename Storage<P>::S;
+  static_assert(sizeof(S) == sizeof(T), "copies move stored values unchanged");
+  constexpr int R = Sh::R, PX = Sh::PX, PY = Sh::PY, NPAD = Sh::NPAD, NT = Sh::NT, NH = Sh::NH;
+  constexpr int NHPER = Sh::NHPER;
+  constexpr int XW = Sh::XW, VE = Sh::VE, NCH = Sh::NCH, NS = Sh::NS, NR = Sh::NR;
+  T* stages = reinterpret_cast<T*>(smem_raw);
+  T* ring = stages + NS * Sh::stage_elems;
+
+  const int nx = d.nx, ny = d.ny, nz = d.nz;
+  const long long plane = d.plane;
+  const S* __restrict__ src = static_cast<const S*>(d.src);
+  S* __restrict__ dst = static_cast<S*>(d.dst);
+  const T n0 = (T)d.n0, G = (T)d.eos.G;
+  const int tiles_x = (nx + BX - 1) / BX;
+  const int tid = threadIdx.x;
+  const int tx = tid % BX, ty = tid / BX;
+  const int ncols = tiles_x * ((ny + BY - 1) / BY);
+
+  const int col = (int)(item % ncols);
+  const int z0 = (int)(item / ncols) * zchunk;
+  const int zc = min(zchunk, nz - z0);
+  const int x0 = (col % tiles_x) * BX, y0 = (col / tiles_x) * BY;
+  const int w = min(BX, nx - x0), h = min(BY, ny - y0);
+  const bool active = tx < w && ty < h;
+  const int rows = h + 2 * R;
+  const int xa = x0 - kBulkApron;
+
+  // copy positions (as in the chunked kernel)
+  constexpr int POS = PY * NCH;
+  constexpr int NG = (2 * POS <= NT) ? 2 : 1;
+  constexpr int NPP = NG == 2 ? 1 : (POS + NT - 1) / NT;
+  constexpr int ISPLIT = NG == 2 ? 10 : Q;
+  const int grp = NG == 2 ? tid / POS : 0;
+  const S* srcp[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) srcp[i] = src + i * plane;
+  int prow[NPP][3], pgx[NPP], psm[NPP];
+  bool pok[NPP];
+#pragma unroll
+  for (int pp = 0; pp < NPP; ++pp) {
+    const int p = NG == 2 ? tid % POS : tid + pp * NT;
+    const int jy = p / NCH, k = p % NCH;
+    pok[pp] = (NG == 2 ? grp < 2 : p < POS) && jy < rows;
+    const int y = wrap(y0 - R + (pok[pp] ? jy : 0), ny);
+    prow[pp][0] = wrap(y + 1, ny) * nx;
+    prow[pp][1] = y * nx;
+    prow[pp][2] = wrap(y - 1, ny) * nx;
+    pgx[pp] = wrap(xa + k * VE, nx);
+    psm[pp] = jy * XW + k * VE;
+  }
+  // density-pass nodes: own column's node (padded (ty + R, tx + R)) and halo ring nodes
+  const int j0 = (ty + R) * PX + (tx + R);
+  const bool valid0 = tx < w + R && ty < h + R;
+  int jh[NHPER];
+  bool validh[NHPER];
+#pragma unroll
+  for (int s = 0; s < NHPER; ++s) {
+    const int hh = tid + s * NT;
+    jh[s] = hh < NH ? halo_node<R, PX, PY>(hh) : 0;
+    validh[s] = hh < NH && (jh[s] % PX) < w + 2 * R && (jh[s] / PX) < rows;
+  }
+  const int nplanes = zc + 2 * R;
+
+  auto issue = [&](int q) {
+    if (q < nplanes) {
+      const int z = wrap(z0 - R + q, nz);
+      const int zo[3] = {wrap(z + 1, nz) * ny * nx, z * ny * nx, wrap(z - 1, nz) * ny * nx};
+      T* st = stages + (q % NS) * Sh::stage_elems;
+#pragma unroll
+      for (int pp = 0; pp < NPP; ++pp) {
+        if (!pok[pp]) continue;
+        if (grp == 0) {
+#pragma unroll
+          for (int i = 0; i < ISPLIT; ++i)
+            cp_async_chunk16(st + i * PY * XW + psm[pp],
+                             srcp[i] + (zo[cz(i) + 1] + prow[pp][cy(i) + 1] + pgx[pp]));
+        } else if (NG == 2) {
+#pragma unroll
+          for (int i = ISPLIT; i < Q; ++i)
+            cp_async_chunk16(st + i * PY * XW + psm[pp],
+                             srcp[i] + (zo[cz(i) + 1] + prow[pp][cy(i) + 1] + pgx[pp]));
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  // moments of the own interior node for the last R + 1 planes: m[0] newest
+  T mdn[R + 1], mjx[R + 1], mjy[R + 1], mjz[R + 1];
+#pragma unroll
+  for (int r = 0; r <= R; ++r) mdn[r] = mjx[r] = mjy[r] = mjz[r] = (T)0;
+
+  __syncthreads();   // the previous item's readers are done with every stage
+#pragma unroll 1
+  for (int q = 0; q < D; ++q) issue(q);
+
+#pragma unroll 1
+  for (int qd = 0; qd < nplanes; ++qd) {
+    cp_async_wait<D - 1>();
+    __syncthreads();
+    issue(qd + D);     // into the stage of plane qd - 1, whose last reads preceded the barrier
+#pragma unroll
+    for (int r = R; r > 0; --r) {
+      mdn[r] = mdn[r - 1];
+      mjx[r] = mjx[r - 1];
+      mjy[r] = mjy[r - 1];
+      mjz[r] = mjz[r - 1];
+    }
+    {  // densities, psi and own moments of plane qd
+      const T* st = stages + (qd % NS) * Sh::stage_elems;
+      T* rs = ring + (qd % NR) * NPAD;
+      if (valid0) {
+        const T* row0 = st + (ty + R) * XW + tx + kBulkApron;
+        T v[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) v[i] = row0[i * PY * XW - cx(i)];
+        T dn, jx, jy, jz;
+        moments(v, dn, jx, jy, jz);
+        rs[j0] = psi_of<T>(n0 + dn, d.eos);
+        mdn[0] = dn;
+        mjx[0] = jx;
+        mjy[0] = jy;
+        mjz[0] = jz;
+      }
+#pragma unroll
+      for (int s = 0; s < NHPER; ++s) {
+        if (!validh[s]) continue;
+        const int hx = jh[s] % PX, hy = jh[s] / PX;
+        const T* row0 = st + hy * XW + hx + kBulkApron - R;
+        T v[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) v[i] = row0[i * PY * XW - cx(i)];
+        rs[jh[s]] = psi_of<T>(n0 + sum19(v), d.eos);
+      }
+    }
+    __syncthreads();
+    const int qc = qd - R;
+    const int k = qc - R;
+    if (k >= 0 && active) {
+      const T* planes[2 * R + 1];
+#pragma unroll
+      for (int dz = -R; dz <= R; ++dz) planes[dz + R] = ring + ((qc + dz) % NR) * NPAD + j0;
+      T Fx, Fy, Fz;
+      sc_force_pairs<T, ST, PX>(planes, G, Fx, Fy, Fz);
+      const T dn = mdn[R];
+      const T n = n0 + dn;
+      const T inv_n = (T)1 / n;
+      const T ux = (mjx[R] + (T)0.5 * Fx) * inv_n;
+      const T uy = (mjy[R] + (T)0.5 * Fy) * inv_n;
+      const T uz = (mjz[R] + (T)0.5 * Fz) * inv_n;
+      T g[Q];     // written, never read, by the unit-tau collision
+      collide<T, true, true>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, (T)1);
+      const long long node = ((long long)(z0 + k) * ny + (y0 + ty)) * nx + (x0 + tx);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) dst[i * plane + node] = (S)g[i];
+    }
+  }
+  cp_async_wait_all();
+}
+
+template <int P, int ST, int BX, int BY, int D>
+__global__ void __launch_bounds__(BX * BY, (async_min_blocks<BX * BY, MomentShape<P, ST, BX, BY, D>::smem_bytes>()))
+lattice_moment_kernel(LatticeDesc d, int zchunk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ncols = ((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
+  const long long items = (long long)ncols * ((d.nz + zchunk - 1) / zchunk);
+#pragma unroll 1
+  for (long long item = blockIdx.x; item < items; item += gridDim.x)
+    moment_process_item<P, ST, BX, BY, D>(d, zchunk, item, smem_raw);
+}
+
+// A batch of tau = 1 lattices (see lattice_async_batch_kernel for the table):
+// every lattice takes the moment kernel's path.
+template <int P, int ST, int BX, int BY, int D>
+__global__ void __launch_bounds__(BX * BY, (async_min_blocks<BX * BY, MomentShape<P, ST, BX, BY, D>::smem_bytes>()))
+lattice_moment_batch_kernel(const BatchEntry* __restrict__ table, const BatchHeader* __restrict__ hdr,
+                            int step) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = hdr->n;
+  const long long total = hdr->total_items;
+#pragma unroll 1
+  for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+    int lo = 0, hi = n - 1;          // last entry with item_begin <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (table[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+    }
+    LatticeDesc d = table[lo].d;
+    if ((table[lo].parity ^ step) & 1) {
+      const void* t = d.src;
+      d.src = d.dst;
+      d.dst = const_cast<void*>(t);
+    }
+    moment_process_item<P, ST, BX, BY, D>(d, table[lo].zchunk, item - table[lo].item_begin, smem_raw);
+  }
+}
+
+}  // namespace lbm

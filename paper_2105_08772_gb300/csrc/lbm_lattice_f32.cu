@@ -6,9 +6,9 @@ cudaError_t launch_lattice_f32(int stencil, int mode, const LatticeDesc& d, Tile
                                const ObsArgs& oa, cudaStream_t s) {
   return dispatch_lattice<kF32>(stencil, mode, d, cfg, oa, s);
 }
-cudaError_t launch_batch_f32(int stencil, bool unit_tau, const BatchEntry* table,
+cudaError_t launch_batch_f32(int stencil, int mode, const BatchEntry* table,
                               const BatchHeader* hdr, int step, bool prepare, int* grid,
                               cudaStream_t s) {
-  return dispatch_batch_stencil<kF32>(stencil, unit_tau, table, hdr, step, prepare, grid, s);
+  return dispatch_batch_stencil<kF32>(stencil, mode, table, hdr, step, prepare, grid, s);
 }
 }  // namespace lbm

@@ -3,6 +3,8 @@
 #pragma once
 
 #include "lbm_kernels_bulk.cuh"
+#include "lbm_kernels_chunk.cuh"
+#include "lbm_kernels_moment.cuh"
 #include "lbm_launch.h"
 
 namespace lbm {
@@ -99,6 +101,99 @@ static cudaError_t launch_bulk_variant(const LatticeDesc& d, int zchunk, bool pr
   return cudaGetLastError();
 }
 
+template <int P, int ST, int BX, int BY, int D, bool UNIT_TAU>
+static cudaError_t launch_chunk_variant(const LatticeDesc& d, int zchunk, bool prepare,
+                                        cudaStream_t s) {
+  using Sh = ChunkShape<P, ST, BX, BY, D>;
+  static_assert(Sh::smem_bytes == chunk_smem_bytes(sizeof(typename Sh::T), Sh::R, BX, BY, D),
+                "host and device disagree on the chunked kernel's shared memory");
+  auto kern = lattice_chunk_kernel<P, ST, BX, BY, D, UNIT_TAU>;
+  static int resident = 0;
+  if (prepare || resident == 0) {
+    cudaError_t e = prepare_persistent(kern, Sh::NT, Sh::smem_bytes, &resident);
+    if (e != cudaSuccess || prepare) return e;
+  }
+  if (d.nx % 4 != 0 || d.nx < BX + 8) return cudaErrorInvalidValue;
+  const long long cols = (long long)((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
+  const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
+  const long long items = cols * ((d.nz + zc - 1) / zc);
+  const long long grid = items < resident ? items : resident;
+  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, zc);
+  return cudaGetLastError();
+}
+
+template <int P, int ST, int BX, int BY, int D>
+static cudaError_t launch_chunk(const LatticeDesc& d, int zchunk, bool prepare, cudaStream_t s) {
+  if (prepare) {
+    cudaError_t e = launch_chunk_variant<P, ST, BX, BY, D, true>(d, 0, true, s);
+    if (e != cudaSuccess) return e;
+    return launch_chunk_variant<P, ST, BX, BY, D, false>(d, 0, true, s);
+  }
+  if (d.omega == 1.0) return launch_chunk_variant<P, ST, BX, BY, D, true>(d, zchunk, false, s);
+  return launch_chunk_variant<P, ST, BX, BY, D, false>(d, zchunk, false, s);
+}
+
+// unit-tau moment kernel; for tau != 1 the chunked kernel of the same shape runs
+template <int P, int ST, int BX, int BY, int D>
+static cudaError_t launch_moment(const LatticeDesc& d, int zchunk, bool prepare, cudaStream_t s) {
+  using Sh = MomentShape<P, ST, BX, BY, D>;
+  static_assert(Sh::smem_bytes == moment_smem_bytes(sizeof(typename Sh::T), Sh::R, BX, BY, D),
+                "host and device disagree on the moment kernel's shared memory");
+  auto kern = lattice_moment_kernel<P, ST, BX, BY, D>;
+  static int resident = 0;
+  if (prepare || resident == 0) {
+    cudaError_t e = prepare_persistent(kern, Sh::NT, Sh::smem_bytes, &resident);
+    if (e == cudaSuccess && prepare) e = launch_chunk<P, ST, BX, BY, D>(d, 0, true, s);
+    if (e != cudaSuccess || prepare) return e;
+  }
+  if (d.omega != 1.0) return launch_chunk<P, ST, BX, BY, D>(d, zchunk, false, s);
+  if (d.nx % 4 != 0 || d.nx < BX + 8) return cudaErrorInvalidValue;
+  const long long cols = (long long)((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
+  const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
+  const long long items = cols * ((d.nz + zc - 1) / zc);
+  const long long grid = items < resident ? items : resident;
+  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, zc);
+  return cudaGetLastError();
+}
+
+template <int P, int ST>
+static cudaError_t dispatch_moment(const LatticeDesc& d, TileCfg c, cudaStream_t s) {
+  if constexpr (P == kF16) {
+    return cudaErrorInvalidValue;
+  } else {
+    const bool prep = c.prepare;
+    if (ST == 4) {
+      if (c.bx == 32 && c.by == 8 && c.depth == 1) return launch_moment<P, 4, 32, 8, 1>(d, c.zchunk, prep, s);
+      if (c.bx == 32 && c.by == 8 && c.depth == 2) return launch_moment<P, 4, 32, 8, 2>(d, c.zchunk, prep, s);
+      if (c.bx == 32 && c.by == 4 && c.depth == 1) return launch_moment<P, 4, 32, 4, 1>(d, c.zchunk, prep, s);
+      if (c.bx == 32 && c.by == 4 && c.depth == 2) return launch_moment<P, 4, 32, 4, 2>(d, c.zchunk, prep, s);
+      if (c.bx == 64 && c.by == 4 && c.depth == 1) return launch_moment<P, 4, 64, 4, 1>(d, c.zchunk, prep, s);
+    } else {
+      if (c.bx == 32 && c.by == 4 && c.depth == 1) return launch_moment<P, ST, 32, 4, 1>(d, c.zchunk, prep, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+}
+
+template <int P, int ST>
+static cudaError_t dispatch_chunk(const LatticeDesc& d, TileCfg c, cudaStream_t s) {
+  if constexpr (P == kF16) {
+    return cudaErrorInvalidValue;
+  } else {
+    const bool prep = c.prepare;
+    if (ST == 4) {
+      if (c.bx == 32 && c.by == 8 && c.depth == 1) return launch_chunk<P, 4, 32, 8, 1>(d, c.zchunk, prep, s);
+      if (c.bx == 32 && c.by == 8 && c.depth == 2) return launch_chunk<P, 4, 32, 8, 2>(d, c.zchunk, prep, s);
+      if (c.bx == 32 && c.by == 4 && c.depth == 1) return launch_chunk<P, 4, 32, 4, 1>(d, c.zchunk, prep, s);
+      if (c.bx == 32 && c.by == 4 && c.depth == 2) return launch_chunk<P, 4, 32, 4, 2>(d, c.zchunk, prep, s);
+      if (c.bx == 64 && c.by == 4 && c.depth == 1) return launch_chunk<P, 4, 64, 4, 1>(d, c.zchunk, prep, s);
+    } else {
+      if (c.bx == 32 && c.by == 4 && c.depth == 1) return launch_chunk<P, ST, 32, 4, 1>(d, c.zchunk, prep, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+}
+
 template <int P, int ST, int BX, int BY, int D>
 static cudaError_t launch_bulk(const LatticeDesc& d, int zchunk, bool prepare, cudaStream_t s) {
   if (prepare) {
@@ -160,28 +255,47 @@ static cudaError_t launch_batch_variant(const BatchEntry* table, const BatchHead
   return cudaGetLastError();
 }
 
-// batches use the pipelined kernel: 32 x 8 tiles for FP32 E4, 32 x 4 otherwise
+template <int P, int ST, int BX, int BY, int D>
+static cudaError_t launch_moment_batch_variant(const BatchEntry* table, const BatchHeader* hdr, int step,
+                                               bool prepare, int* grid, cudaStream_t s) {
+  using Sh = MomentShape<P, ST, BX, BY, D>;
+  auto kern = lattice_moment_batch_kernel<P, ST, BX, BY, D>;
+  static int resident = 0;
+  if (prepare || resident == 0) {
+    cudaError_t e = prepare_persistent(kern, Sh::NT, Sh::smem_bytes, &resident);
+    if (e != cudaSuccess) return e;
+  }
+  if (grid) *grid = resident;
+  if (prepare) return cudaSuccess;
+  kern<<<(unsigned)resident, Sh::NT, Sh::smem_bytes, s>>>(table, hdr, step);
+  return cudaGetLastError();
+}
+
+// batches: the moment kernel when every lattice allows it, else the pipelined
+// kernel; 32 x 8 tiles for FP32 E4, 32 x 4 otherwise (batch_tile)
 template <int P, int ST>
-static cudaError_t dispatch_batch(bool unit_tau, const BatchEntry* table, const BatchHeader* hdr,
+static cudaError_t dispatch_batch(int mode, const BatchEntry* table, const BatchHeader* hdr,
                                   int step, bool prepare, int* grid, cudaStream_t s) {
   if constexpr (P == kF16) {
     return cudaErrorInvalidValue;
   } else if constexpr (P == kF32 && ST == 4) {
-    if (unit_tau) return launch_batch_variant<P, ST, 32, 8, 1, false>(table, hdr, step, prepare, grid, s);
+    if (mode == kBatchMoment) return launch_moment_batch_variant<P, ST, 32, 8, 1>(table, hdr, step, prepare, grid, s);
+    if (mode == kBatchUnitTau) return launch_batch_variant<P, ST, 32, 8, 1, false>(table, hdr, step, prepare, grid, s);
     return launch_batch_variant<P, ST, 32, 8, 1, true>(table, hdr, step, prepare, grid, s);
   } else {
-    if (unit_tau) return launch_batch_variant<P, ST, 32, 4, 1, false>(table, hdr, step, prepare, grid, s);
+    if (mode == kBatchMoment) return launch_moment_batch_variant<P, ST, 32, 4, 1>(table, hdr, step, prepare, grid, s);
+    if (mode == kBatchUnitTau) return launch_batch_variant<P, ST, 32, 4, 1, false>(table, hdr, step, prepare, grid, s);
     return launch_batch_variant<P, ST, 32, 4, 1, true>(table, hdr, step, prepare, grid, s);
   }
 }
 
 template <int P>
-static cudaError_t dispatch_batch_stencil(int stencil, bool unit_tau, const BatchEntry* table,
+static cudaError_t dispatch_batch_stencil(int stencil, int mode, const BatchEntry* table,
                                           const BatchHeader* hdr, int step, bool prepare, int* grid,
                                           cudaStream_t s) {
-  if (stencil == 4) return dispatch_batch<P, 4>(unit_tau, table, hdr, step, prepare, grid, s);
-  if (stencil == 6) return dispatch_batch<P, 6>(unit_tau, table, hdr, step, prepare, grid, s);
-  if (stencil == 8) return dispatch_batch<P, 8>(unit_tau, table, hdr, step, prepare, grid, s);
+  if (stencil == 4) return dispatch_batch<P, 4>(mode, table, hdr, step, prepare, grid, s);
+  if (stencil == 6) return dispatch_batch<P, 6>(mode, table, hdr, step, prepare, grid, s);
+  if (stencil == 8) return dispatch_batch<P, 8>(mode, table, hdr, step, prepare, grid, s);
   return cudaErrorInvalidValue;
 }
 
@@ -221,6 +335,18 @@ static cudaError_t dispatch_lattice(int stencil, int mode, const LatticeDesc& d,
     if (stencil == 4) return dispatch_bulk<P, 4>(d, c, s);
     if (stencil == 6) return dispatch_bulk<P, 6>(d, c, s);
     if (stencil == 8) return dispatch_bulk<P, 8>(d, c, s);
+    return cudaErrorInvalidValue;
+  }
+  if (mode == kModeStep && c.kind == 5) {
+    if (stencil == 4) return dispatch_moment<P, 4>(d, c, s);
+    if (stencil == 6) return dispatch_moment<P, 6>(d, c, s);
+    if (stencil == 8) return dispatch_moment<P, 8>(d, c, s);
+    return cudaErrorInvalidValue;
+  }
+  if (mode == kModeStep && c.kind == 4) {
+    if (stencil == 4) return dispatch_chunk<P, 4>(d, c, s);
+    if (stencil == 6) return dispatch_chunk<P, 6>(d, c, s);
+    if (stencil == 8) return dispatch_chunk<P, 8>(d, c, s);
     return cudaErrorInvalidValue;
   }
   if (mode == kModeStep && c.kind == 1) {

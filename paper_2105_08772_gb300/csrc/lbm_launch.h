@@ -74,6 +74,30 @@ constexpr int kBulkE4[kNumBulkE4][3] = {{32, 8, 1}, {32, 4, 1}, {64, 4, 1}, {32,
 constexpr int kNumBulkWide = 1;
 constexpr int kBulkWide[kNumBulkWide][3] = {{32, 4, 1}};
 
+// dynamic shared memory of the chunked kernel: (R + 1 + depth) stages of
+// 19 x (by + 2R) rows of bx + 8 elements, psi ring of 2R + 1 padded planes
+constexpr size_t chunk_smem_bytes(size_t elem, int R, int bx, int by, int depth) {
+  return elem * ((size_t)(R + 1 + depth) * Q * (by + 2 * R) * (bx + 8) +
+                 (size_t)(2 * R + 1) * (bx + 2 * R) * (by + 2 * R));
+}
+// (bx, by, depth) compiled for the chunked step kernel (kind 4)
+constexpr int kNumChunkE4 = 5;
+constexpr int kChunkE4[kNumChunkE4][3] = {{32, 8, 1}, {32, 8, 2}, {32, 4, 1}, {32, 4, 2}, {64, 4, 1}};
+constexpr int kNumChunkWide = 1;
+constexpr int kChunkWide[kNumChunkWide][3] = {{32, 4, 1}};
+
+// dynamic shared memory of the unit-tau moment kernel: 1 + depth stages, psi ring
+constexpr size_t moment_smem_bytes(size_t elem, int R, int bx, int by, int depth) {
+  return elem * ((size_t)(1 + depth) * Q * (by + 2 * R) * (bx + 8) +
+                 (size_t)(2 * R + 1) * (bx + 2 * R) * (by + 2 * R));
+}
+// (bx, by, depth) compiled for the moment kernel (kind 5; tau = 1, else the
+// chunked kernel of the same shape runs)
+constexpr int kNumMomentE4 = 5;
+constexpr int kMomentE4[kNumMomentE4][3] = {{32, 8, 1}, {32, 8, 2}, {32, 4, 1}, {32, 4, 2}, {64, 4, 1}};
+constexpr int kNumMomentWide = 1;
+constexpr int kMomentWide[kNumMomentWide][3] = {{32, 4, 1}};
+
 constexpr size_t kMaxSmemPerCta = 227 * 1024;   // opt-in limit of one CTA on sm_103
 
 // number of CTAs (= FieldPartial records) a kind-0 lattice launch uses
@@ -87,19 +111,22 @@ struct BatchEntry;
 struct BatchHeader;
 // the tile every batch of this precision / stencil uses, and its launch;
 // prepare readies the kernel outside capture and reports the grid it uses
-inline TileCfg batch_tile(int prec, int stencil) {
+// batch kernel modes: lattices with mixed tau, all tau = 1, or all tau = 1 with
+// boxes the moment kernel takes (nx % 4 == 0, nx >= tile width + 8)
+enum BatchMode : int { kBatchMixedTau = 0, kBatchUnitTau = 1, kBatchMoment = 2 };
+inline TileCfg batch_tile(int prec, int stencil, int mode) {
   TileCfg t{32, (prec == kF32 && stencil == 4) ? 8 : 4, 0};
-  t.kind = 1;
+  t.kind = mode == kBatchMoment ? 5 : 1;
   return t;
 }
-cudaError_t launch_batch_f64(int stencil, bool unit_tau, const BatchEntry* table, const BatchHeader* hdr,
+cudaError_t launch_batch_f64(int stencil, int mode, const BatchEntry* table, const BatchHeader* hdr,
                              int step, bool prepare, int* grid, cudaStream_t s);
-cudaError_t launch_batch_f32(int stencil, bool unit_tau, const BatchEntry* table, const BatchHeader* hdr,
+cudaError_t launch_batch_f32(int stencil, int mode, const BatchEntry* table, const BatchHeader* hdr,
                              int step, bool prepare, int* grid, cudaStream_t s);
-inline cudaError_t launch_batch(int prec, int stencil, bool unit_tau, const BatchEntry* table,
+inline cudaError_t launch_batch(int prec, int stencil, int mode, const BatchEntry* table,
                                 const BatchHeader* hdr, int step, bool prepare, int* grid, cudaStream_t s) {
-  if (prec == kF64) return launch_batch_f64(stencil, unit_tau, table, hdr, step, prepare, grid, s);
-  if (prec == kF32) return launch_batch_f32(stencil, unit_tau, table, hdr, step, prepare, grid, s);
+  if (prec == kF64) return launch_batch_f64(stencil, mode, table, hdr, step, prepare, grid, s);
+  if (prec == kF32) return launch_batch_f32(stencil, mode, table, hdr, step, prepare, grid, s);
   return cudaErrorInvalidValue;
 }
 

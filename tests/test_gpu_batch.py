@@ -39,6 +39,34 @@ def test_batch_equals_single_lattice_runs(prec, tile):
         assert list(ob.com) == list(ref.com)
 
 
+RUNS_UNIT_TAU = [  # tau = 1 and nx % 4 == 0, nx >= 40: the batch takes the moment kernel
+    ((40, 32, 28), 1.0, -5.5, 7.0, 0.12, 1.89),
+    ((48, 40, 36), 1.0, -5.0, 9.0, 1.89, 0.12),
+    ((44, 20, 13), 1.0, -4.6, 5.0, 1.70, 0.25),
+]
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_moment_batch_equals_single_lattice_runs(prec):
+    """All-tau-1 batches run the moment kernel; each lattice still evolves bitwise as
+    it does alone (default tile)."""
+    steps, check = 384, 128
+    b = P.Batch(2, (48, 40, 36), prec=prec)
+    ids = [b.enqueue(box, tau=tau, G=G, R=R, rho_in=ri, rho_out=ro)
+           for box, tau, G, R, ri, ro in RUNS_UNIT_TAU]
+    b.run(max_steps=steps, check_every=check, tol_dP_rel=-1.0, tol_du=-1.0)
+    for rid, (box, tau, G, R, ri, ro) in zip(ids, RUNS_UNIT_TAU):
+        st, ob = b.result(rid)
+        assert st == P._lib.LBM_ENOTCONV and ob.steps == steps, (rid, st, ob.steps)
+        lat = P.Lattice(*box, tau=tau, G=G, prec=prec)
+        lat.init_drop((box[0] // 2, box[1] // 2, box[2] // 2), R, ri, ro)
+        lat.step(steps)
+        ref = lat.observables()
+        for k in STATE_KEYS:
+            a, r = getattr(ob, k), getattr(ref, k)
+            assert (a == r) or (np.isnan(a) and np.isnan(r)), (rid, k, a, r)
+
+
 def test_batch_droplets_converge_and_small_bubbles_collapse():
     """32^3 droplets of R = 8 converge to a centred droplet; bubbles that small dissolve
     into the liquid, which the runs must report as COLLAPSED (status bit 1)."""

@@ -313,3 +313,75 @@ def test_row_bulk_kernel_wide_stencil_and_tau():
     a.step(40)
     ref = lbm3d.run(f0, oracle_model(stencil="E6", tau=0.8), 40)
     assert np.max(np.abs(a.get_populations() - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("prec,code", [(p, c) for p in ("f64", "f32")
+                                       for c in (432080001, 432040001, 464040001, 432080081)]
+                         + [("f32", 432080002), ("f32", 432040002)])
+def test_chunked_kernel_matches_pipelined_kernel_and_oracle(prec, code):
+    """The chunked kernel (kind 4: 16-byte row chunks) stages the same values as the
+    pipelined kernel: bitwise-equal fields, and the oracle's.  nx = 72 with 32-wide
+    tiles has a ragged last column whose staged rows wrap at the right end; ny and
+    nz are ragged too."""
+    shape = (13, 22, 72)
+    f0 = inputs.random_populations(shape, seed=25)
+    a = lattice(shape, prec=prec)
+    a.set_populations(f0)
+    a.set_tile(code)
+    a.step(130)
+    b = lattice(shape, prec=prec)
+    b.set_populations(f0)
+    b.set_tile(132080001)
+    b.step(130)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    if prec == "f64":
+        ref = lbm3d.run(f0, oracle_model(), 130)
+        assert np.max(np.abs(a.get_populations() - ref)) < 1e-12
+
+
+def test_chunked_kernel_wide_stencil_and_tau():
+    shape = (9, 10, 40)
+    f0 = inputs.random_populations(shape, seed=26)
+    a = lattice(shape, stencil="E6", tau=0.8)
+    a.set_populations(f0)
+    a.set_tile(432040001)
+    a.step(40)
+    ref = lbm3d.run(f0, oracle_model(stencil="E6", tau=0.8), 40)
+    assert np.max(np.abs(a.get_populations() - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("prec,code,tau", [(p, c, 1.0) for p in ("f64", "f32")
+                                           for c in (532080001, 532040001, 564040001, 532080081)]
+                         + [("f32", 532080002, 1.0), ("f32", 532040002, 1.0),
+                            ("f64", 532080001, 0.8), ("f32", 532040002, 0.8)])
+def test_moment_kernel_matches_pipelined_kernel_and_oracle(prec, code, tau):
+    """The unit-tau moment kernel (kind 5) keeps only n and j of a node between its
+    density pass and its collision; for tau = 1 that is all the collision uses, so
+    fields are bitwise equal to the pipelined kernel's, and to the oracle's.  For
+    tau != 1 the same tile code runs the chunked kernel.  Ragged x, y and z."""
+    shape = (13, 22, 72)
+    f0 = inputs.random_populations(shape, seed=27)
+    a = lattice(shape, prec=prec, tau=tau)
+    a.set_populations(f0)
+    a.set_tile(code)
+    a.step(130)
+    b = lattice(shape, prec=prec, tau=tau)
+    b.set_populations(f0)
+    b.set_tile(132080001)
+    b.step(130)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    if prec == "f64":
+        ref = lbm3d.run(f0, oracle_model(tau=tau), 130)
+        assert np.max(np.abs(a.get_populations() - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("stencil", ["E6", "E8"])
+def test_moment_kernel_wide_stencils(stencil):
+    shape = (9, 10, 40)
+    f0 = inputs.random_populations(shape, seed=28)
+    a = lattice(shape, stencil=stencil)
+    a.set_populations(f0)
+    a.set_tile(532040001)
+    a.step(40)
+    ref = lbm3d.run(f0, oracle_model(stencil=stencil), 40)
+    assert np.max(np.abs(a.get_populations() - ref)) < 1e-12
