@@ -64,7 +64,7 @@ def measured_traffic(prec):
     """DRAM bytes per launch of the step kernel from the committed ncu summary, or None
     when there is none for this precision or the kernel sources changed since."""
     import hashlib
-    summary = ROOT / "profiles" / f"lattice_async_{prec}_128.md"
+    summary = ROOT / "profiles" / f"lattice_moment_{prec}_128.md"
     if not summary.exists():
         return None
     fields = {}
@@ -231,6 +231,10 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-sweep-leg", action="store_true")
     ap.add_argument("--no-large-leg", action="store_true")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="build the 128^3 droplet lattice, run two single steps and exit "
+                         "(a small, fixed launch sequence for ncu captures)")
+    ap.add_argument("--tile", type=int, default=0, help="tile code for --kernel-only (0: default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -246,6 +250,17 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     import paper_2105_08772_gb300 as P
+
+    if args.kernel_only:
+        lat = P.Lattice(SIZE, SIZE, SIZE, tau=TAU, G=G, psi="one_minus_exp", stencil="E4", prec=args.prec)
+        lat.init_drop((SIZE // 2,) * 3, RADIUS, RHO_L, RHO_G)
+        if args.tile:
+            lat.set_tile(args.tile)
+        lat.step(1)
+        lat.step(1)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_only": True, "tile": lat.get_tile(), "prec": args.prec}))
+        return
 
     dev = torch.cuda.current_device()
     stream = torch.cuda.Stream()
