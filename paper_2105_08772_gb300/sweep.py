@@ -172,6 +172,46 @@ def run_plain(runs, coex, prec: str = "f64", stencil: str = "E4", max_steps: int
     return outs, time.perf_counter() - t0, lu
 
 
+def shard(runs, rank: int, world: int):
+    """The runs of one rank when the sweep is spread over `world` processes (one GPU
+    each): round-robin over the largest-first plan, so every rank gets a similar mix
+    of box sizes.  The lattices are independent; nothing is exchanged while they run."""
+    if not 0 <= rank < world:
+        raise ValueError(f"rank {rank} outside world {world}")
+    return list(runs[rank::world])
+
+
+def gather_outcomes(local, group=None):
+    """All ranks' outcomes on every rank (control plane only: small Python objects
+    through torch.distributed.all_gather_object), in rank order."""
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size(group) == 1:
+        return list(local)
+    parts = [None] * dist.get_world_size(group)
+    dist.all_gather_object(parts, [(asdict(o.run), o.status, dict(o.obs)) for o in local], group=group)
+    return [Outcome(Run(**r), st, obs) for part in parts for (r, st, obs) in part]
+
+
+def gather_outcomes_counts(count: int, group=None) -> list:
+    """Every rank's count (lattice updates), in rank order."""
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size(group) == 1:
+        return [count]
+    parts = [None] * dist.get_world_size(group)
+    dist.all_gather_object(parts, int(count), group=group)
+    return parts
+
+
+def max_over_ranks(seconds: float, group=None) -> float:
+    """The slowest rank's wall time (the job's time)."""
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size(group) == 1:
+        return seconds
+    parts = [None] * dist.get_world_size(group)
+    dist.all_gather_object(parts, float(seconds), group=group)
+    return max(parts)
+
+
 @dataclass
 class TolmanResult:
     G: float
@@ -253,21 +293,38 @@ def main(argv=None) -> dict:
     ap.add_argument("--per-R", type=float, default=4.0)
     ap.add_argument("--plain", default="", help="couplings also run one lattice at a time in FP64")
     ap.add_argument("--out", default="")
+    ap.add_argument("--distributed", action="store_true",
+                    help="one process per GPU under torchrun: the runs are sharded over the ranks")
     a = ap.parse_args(argv)
+    rank, world = 0, 1
+    if a.distributed:
+        import os
+
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("gloo")   # only small Python objects travel
+        rank, world = dist.get_rank(), dist.get_world_size()
     couplings = tuple(float(g) for g in a.couplings.split(","))
     radii = _parse_radii(a.radii)
     runs = plan(couplings, radii, psi=a.psi, L_min=a.L_min, per_R=a.per_R)
     t0 = time.perf_counter()
     coex = coexistence(couplings, psi=a.psi)
     t_flat = time.perf_counter() - t0
-    outs, wall, lu = run_batched(runs, coex, slots=a.slots, prec=a.prec, max_steps=a.max_steps)
+    mine = shard(runs, rank, world)
+    outs, wall, lu = run_batched(mine, coex, slots=a.slots, prec=a.prec, max_steps=a.max_steps)
+    if world > 1:
+        outs = gather_outcomes(outs)
+        wall = max_over_ranks(wall)
+        lu = int(sum(gather_outcomes_counts(lu)))
     fit = tolman(outs, coex)
     report = {"runs": len(runs), "usable": sum(o.usable for o in outs), "flat_wall_s": t_flat,
+              "ranks": world,
               "batched": {"prec": a.prec, "slots": a.slots, "wall_s": wall, "lattice_updates": lu,
                           "MLUPS": lu / wall / 1e6},
               "coexistence": {str(G): v for G, v in coex.items()},
               "fit": {str(G): asdict(r) for G, r in fit.items()}}
-    if a.plain:
+    if a.plain and rank == 0 and world == 1:
         pc = tuple(float(g) for g in a.plain.split(","))
         sub = [r for r in runs if r.G in pc]
         sub_b = [o for o in outs if o.run.G in pc]
@@ -287,6 +344,8 @@ def main(argv=None) -> dict:
                           **{k: o.obs[k] for k in ("R_e", "R_s", "sigma_s", "dP", "n_in", "n_out",
                                                    "steps", "status_bits", "criterion")}}
                          for o in outs]
+    if rank != 0:
+        return report
     text = json.dumps(report, indent=1)
     if a.out:
         with open(a.out, "w") as f:
