@@ -6,10 +6,11 @@
 // through n and the momentum j = sum_i xi_i f_i (u = (j + F/2)/n, Eq. (7)).
 // The collision of plane z therefore needs, from its stage, just four numbers
 // per node -- and those can be formed in the same pass that forms the density
-// for psi.  The kernel keeps them in registers for the R planes until psi of
-// plane z + R exists, so a population stage is free as soon as its densities
-// are formed: NS = 1 + D stages instead of R + 1 + D.  The smaller footprint
-// fits more CTAs per SM.
+// for psi.  The kernel keeps them in registers until psi of plane z + R exists,
+// so a population stage is free as soon as its densities are formed: NS = 1 + D
+// stages instead of R + 1 + D.  The smaller footprint fits more CTAs per SM, and
+// one spare psi plane lets a plane's densities and an earlier plane's collision
+// share one barrier.
 //
 // Copies: the 16-byte row chunks of the chunked kernel (lbm_kernels_chunk.cuh).
 // Thread roles in the density pass: each thread forms its own column's padded
@@ -37,7 +38,7 @@ struct MomentShape {
   static constexpr int VE = 16 / (int)sizeof(T);
   static constexpr int NCH = XW / VE;
   static constexpr int NS = 1 + D;
-  static constexpr int NR = 2 * R + 1;
+  static constexpr int NR = 2 * R + 2;                 // psi planes (one spare: one barrier per plane)
   static constexpr size_t stage_elems = (size_t)Q * PY * XW;
   static constexpr size_t smem_bytes = sizeof(T) * (NS * stage_elems + NR * NPAD);
   static_assert(R + 1 <= kBulkApron, "apron must cover the pull of the halo");
@@ -147,28 +148,34 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
     cp_async_commit();
   };
 
-  // moments of the own interior node for the last R + 1 planes: m[0] newest
-  T mdn[R + 1], mjx[R + 1], mjy[R + 1], mjz[R + 1];
+  // moments of the own interior node for the last R + 2 planes: m[0] newest
+  T mdn[R + 2], mjx[R + 2], mjy[R + 2], mjz[R + 2];
 #pragma unroll
-  for (int r = 0; r <= R; ++r) mdn[r] = mjx[r] = mjy[r] = mjz[r] = (T)0;
+  for (int r = 0; r <= R + 1; ++r) mdn[r] = mjx[r] = mjy[r] = mjz[r] = (T)0;
 
-  __syncthreads();   // the previous item's readers are done with every stage
+  __syncthreads();   // the previous item's readers are done with every stage and psi plane
 #pragma unroll 1
   for (int q = 0; q < D; ++q) issue(q);
 
+  // One barrier per plane.  Iteration qd forms the densities of plane qd and
+  // collides plane qc = qd - 1 - R, whose psi neighbours qc - R .. qc + R = qd - 1
+  // were all formed before this iteration's barrier.  The density pass writes psi
+  // slot qd % (2R + 2), which none of those 2R + 1 planes occupies; the stage it
+  // reads is not the one issue() refills (that held plane qd - 1, read before the
+  // barrier).  One extra iteration collides the last plane.
 #pragma unroll 1
-  for (int qd = 0; qd < nplanes; ++qd) {
+  for (int qd = 0; qd <= nplanes; ++qd) {
     cp_async_wait<D - 1>();
     __syncthreads();
-    issue(qd + D);     // into the stage of plane qd - 1, whose last reads preceded the barrier
+    issue(qd + D);
 #pragma unroll
-    for (int r = R; r > 0; --r) {
+    for (int r = R + 1; r > 0; --r) {
       mdn[r] = mdn[r - 1];
       mjx[r] = mjx[r - 1];
       mjy[r] = mjy[r - 1];
       mjz[r] = mjz[r - 1];
     }
-    {  // densities, psi and own moments of plane qd
+    if (qd < nplanes) {  // densities, psi and own moments of plane qd
       const T* st = stages + (qd % NS) * Sh::stage_elems;
       T* rs = ring + (qd % NR) * NPAD;
       if (valid0) {
@@ -195,8 +202,7 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
         rs[jh[s]] = psi_of<T>(n0 + sum19(v), d.eos);
       }
     }
-    __syncthreads();
-    const int qc = qd - R;
+    const int qc = qd - 1 - R;
     const int k = qc - R;
     if (k >= 0 && active) {
       const T* planes[2 * R + 1];
@@ -204,12 +210,12 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
       for (int dz = -R; dz <= R; ++dz) planes[dz + R] = ring + ((qc + dz) % NR) * NPAD + j0;
       T Fx, Fy, Fz;
       sc_force_pairs<T, ST, PX>(planes, G, Fx, Fy, Fz);
-      const T dn = mdn[R];
+      const T dn = mdn[R + 1];
       const T n = n0 + dn;
       const T inv_n = (T)1 / n;
-      const T ux = (mjx[R] + (T)0.5 * Fx) * inv_n;
-      const T uy = (mjy[R] + (T)0.5 * Fy) * inv_n;
-      const T uz = (mjz[R] + (T)0.5 * Fz) * inv_n;
+      const T ux = (mjx[R + 1] + (T)0.5 * Fx) * inv_n;
+      const T uy = (mjy[R + 1] + (T)0.5 * Fy) * inv_n;
+      const T uz = (mjz[R + 1] + (T)0.5 * Fz) * inv_n;
       T g[Q];     // written, never read, by the unit-tau collision
       collide<T, true, true>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, (T)1);
       const long long node = ((long long)(z0 + k) * ny + (y0 + ty)) * nx + (x0 + tx);

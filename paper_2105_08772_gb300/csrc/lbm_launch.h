@@ -87,9 +87,10 @@ constexpr int kNumChunkWide = 1;
 constexpr int kChunkWide[kNumChunkWide][3] = {{32, 4, 1}};
 
 // dynamic shared memory of the unit-tau moment kernel: 1 + depth stages, psi ring
+// of 2R + 2 padded planes
 constexpr size_t moment_smem_bytes(size_t elem, int R, int bx, int by, int depth) {
   return elem * ((size_t)(1 + depth) * Q * (by + 2 * R) * (bx + 8) +
-                 (size_t)(2 * R + 1) * (bx + 2 * R) * (by + 2 * R));
+                 (size_t)(2 * R + 2) * (bx + 2 * R) * (by + 2 * R));
 }
 // (bx, by, depth) compiled for the moment kernel (kind 5; tau = 1, else the
 // chunked kernel of the same shape runs)

@@ -21,7 +21,10 @@ Two ways to run the same list of problems:
 Everything runs on the GPU through liblbm.so; this module only plans the runs,
 calls the library and collects the results.
 
-Command line:  python -m paper_2105_08772_gb300.sweep --couplings -5.0 --radii 6:40:2
+Command lines:  python -m paper_2105_08772_gb300.sweep --couplings -5.0 --radii 6:40:2
+                python -m paper_2105_08772_gb300.sweep --paper --max-L 157
+(--paper: the paper's own sweep, 12 reduced couplings x 2 pseudopotentials x odd
+boxes with R = L/4, and the power law delta = A eps^lambda of Sec. IV.)
 """
 from __future__ import annotations
 
@@ -38,6 +41,21 @@ from .lbm import Batch, Lattice, flat_interface, lbm_tolman_fit
 
 RADII = tuple(range(6, 41, 2))
 COUPLINGS = (-4.6, -5.0, -5.5, -6.0)
+
+# the paper's own sweep (Sec. IV): reduced couplings G/G_c - 1, odd box sides, R = L/4
+PAPER_EPS = (0.029, 0.033, 0.038, 0.045, 0.056, 0.070, 0.079, 0.091, 0.119, 0.159, 0.215, 0.293)
+PAPER_L = (41, 43, 47, 51, 55, 61, 67, 77, 87, 103, 123, 157, 213, 335)
+PAPER_PSI = ("exp_inv", "one_minus_exp")
+
+
+def critical_coupling(psi: str) -> float:
+    """G_c of Sec. IV: G_c c_s^2 = -2.463 (psi = exp(-1/n), G_c = -e^2) and -1.333
+    (psi = 1 - exp(-n), G_c = -4)."""
+    if psi == "exp_inv":
+        return -math.e ** 2
+    if psi == "one_minus_exp":
+        return -4.0
+    raise ValueError(f"no closed-form G_c for psi {psi!r}")
 
 # lbm_obs.status_bits that disqualify a run from the fits
 _BAD_BITS = 1 | 2 | 4 | 8 | 16     # no sigma minimum, collapsed, off centre, non-finite, timeout
@@ -92,6 +110,33 @@ def plan(couplings=COUPLINGS, radii=RADII, psi: str = "one_minus_exp", kinds=("d
             for G in couplings for k in kinds for R in radii]
     runs.sort(key=lambda r: (-r.L, r.G, r.bubble, r.R))
     return runs
+
+
+def plan_paper(eps=PAPER_EPS, psis=PAPER_PSI, sizes=PAPER_L, kinds=("drop", "bubble"),
+               tau: float = 1.0) -> list[Run]:
+    """The paper's sweep: for each psi and reduced coupling eps, G = G_c (1 + eps), and
+    for each odd side L a droplet and a bubble of initial radius R = L/4 centred on the
+    node (L // 2, L // 2, L // 2).  Largest box first."""
+    runs = [Run(critical_coupling(p) * (1.0 + e), k == "bubble", L / 4.0, int(L), p, tau)
+            for p in psis for e in eps for k in kinds for L in sizes]
+    runs.sort(key=lambda r: (-r.L, r.psi, r.G, r.bubble))
+    return runs
+
+
+def reduced_coupling(run: Run) -> float:
+    return run.G / critical_coupling(run.psi) - 1.0
+
+
+def power_law(eps, delta) -> tuple[float, float]:
+    """(A, lambda) of delta = A eps^lambda by least squares in log-log (Sec. IV finds
+    lambda close to -1); points with delta <= 0 are left out."""
+    e = np.asarray(eps, dtype=np.float64)
+    d = np.asarray(delta, dtype=np.float64)
+    keep = (e > 0) & (d > 0)
+    if keep.sum() < 2:
+        return float("nan"), float("nan")
+    lam, logA = np.polyfit(np.log(e[keep]), np.log(d[keep]), 1)
+    return float(np.exp(logA)), float(lam)
 
 
 def coexistence(couplings, psi: str = "one_minus_exp", stencil: str = "E4", Lx: int = 100,
@@ -293,6 +338,9 @@ def main(argv=None) -> dict:
     ap.add_argument("--per-R", type=float, default=4.0)
     ap.add_argument("--plain", default="", help="couplings also run one lattice at a time in FP64")
     ap.add_argument("--out", default="")
+    ap.add_argument("--paper", action="store_true",
+                    help="the paper's sweep: 12 reduced couplings x 2 psi x odd L (see --max-L)")
+    ap.add_argument("--max-L", type=int, default=335, help="largest box side of --paper")
     ap.add_argument("--distributed", action="store_true",
                     help="one process per GPU under torchrun: the runs are sharded over the ranks")
     a = ap.parse_args(argv)
@@ -305,11 +353,17 @@ def main(argv=None) -> dict:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("gloo")   # only small Python objects travel
         rank, world = dist.get_rank(), dist.get_world_size()
-    couplings = tuple(float(g) for g in a.couplings.split(","))
-    radii = _parse_radii(a.radii)
-    runs = plan(couplings, radii, psi=a.psi, L_min=a.L_min, per_R=a.per_R)
     t0 = time.perf_counter()
-    coex = coexistence(couplings, psi=a.psi)
+    if a.paper:
+        runs = plan_paper(sizes=tuple(L for L in PAPER_L if L <= a.max_L))
+        coex = {}
+        for p in PAPER_PSI:
+            coex.update(coexistence(sorted({r.G for r in runs if r.psi == p}), psi=p))
+    else:
+        couplings = tuple(float(g) for g in a.couplings.split(","))
+        radii = _parse_radii(a.radii)
+        runs = plan(couplings, radii, psi=a.psi, L_min=a.L_min, per_R=a.per_R)
+        coex = coexistence(couplings, psi=a.psi)
     t_flat = time.perf_counter() - t0
     mine = shard(runs, rank, world)
     outs, wall, lu = run_batched(mine, coex, slots=a.slots, prec=a.prec, max_steps=a.max_steps)
@@ -324,6 +378,20 @@ def main(argv=None) -> dict:
                           "MLUPS": lu / wall / 1e6},
               "coexistence": {str(G): v for G, v in coex.items()},
               "fit": {str(G): asdict(r) for G, r in fit.items()}}
+    if a.paper:
+        rows = []
+        for G, f in sorted(fit.items()):
+            run = next(r for r in runs if r.G == G)
+            rows.append({"psi": run.psi, "eps": reduced_coupling(run), "G": G, "delta": f.delta_lin,
+                         "sigma0": f.sigma0_lin, "sigma0_flat": f.sigma0_flat,
+                         "delta_quadratic": f.delta, "delta_hat0": f.delta_hat0, "n_used": f.n_used})
+        report["paper"] = {"per_coupling": rows}
+        for p in PAPER_PSI + ("both",):
+            sel = [r for r in rows if p == "both" or r["psi"] == p]
+            A, lam = power_law([r["eps"] for r in sel], [r["delta"] for r in sel])
+            Ah, lamh = power_law([r["eps"] for r in sel], [r["delta_hat0"] for r in sel])
+            report["paper"][f"power_law_{p}"] = {"A": A, "lambda": lam, "A_hat": Ah, "lambda_hat": lamh,
+                                                 "couplings": len(sel)}
     if a.plain and rank == 0 and world == 1:
         pc = tuple(float(g) for g in a.plain.split(","))
         sub = [r for r in runs if r.G in pc]
@@ -339,7 +407,7 @@ def main(argv=None) -> dict:
                                     "MLUPS": lu_s / wall_s / 1e6}
         report["batched_vs_plain"] = {"fit": {str(G): v for G, v in compare(fit, fit_p).items()},
                                       "runs": compare_runs(sub_b, outs_p)}
-    report["per_run"] = [{"G": o.run.G, "bubble": o.run.bubble, "R": o.run.R, "L": o.run.L,
+    report["per_run"] = [{"psi": o.run.psi, "G": o.run.G, "bubble": o.run.bubble, "R": o.run.R, "L": o.run.L,
                           "status": o.status, "usable": o.usable,
                           **{k: o.obs[k] for k in ("R_e", "R_s", "sigma_s", "dP", "n_in", "n_out",
                                                    "steps", "status_bits", "criterion")}}

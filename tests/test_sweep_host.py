@@ -73,3 +73,24 @@ def test_tolman_needs_enough_runs_and_compare():
     r = S.compare(a, b)[-5.0]
     assert r["sigma0"] == pytest.approx(0.001 / 1.001) and r["delta"] == pytest.approx(0.0005 / 0.5005)
     assert r["delta_hat0"] == 0.0
+
+
+def test_paper_plan_and_couplings():
+    """Sec. IV: G = G_c (1 + eps) with G_c = -e^2 and -4; odd L; R = L/4."""
+    runs = S.plan_paper()
+    assert len(runs) == 2 * 12 * 2 * 14
+    assert all(r.L % 2 == 1 and r.R == r.L / 4 for r in runs)
+    eps = sorted({round(S.reduced_coupling(r), 12) for r in runs if r.psi == "exp_inv"})
+    assert eps == sorted(S.PAPER_EPS)
+    assert S.critical_coupling("exp_inv") * (1 / 3) == pytest.approx(-2.463, abs=1e-3)
+    assert S.critical_coupling("one_minus_exp") * (1 / 3) == pytest.approx(-1.333, abs=1e-3)
+    assert runs[0].L == 335
+
+
+def test_power_law_recovers_exponent():
+    import numpy as np
+    e = np.array(S.PAPER_EPS)
+    A, lam = S.power_law(e, 0.3 * e ** -1.0)
+    assert A == pytest.approx(0.3, rel=1e-12) and lam == pytest.approx(-1.0, abs=1e-12)
+    A, lam = S.power_law([0.1, 0.2, 0.3], [-1.0, 2.0, 1.0])   # non-positive delta left out
+    assert lam == pytest.approx(np.log(0.5) / np.log(1.5))
