@@ -386,6 +386,18 @@ def main(argv=None) -> dict:
                          "sigma0": f.sigma0_lin, "sigma0_flat": f.sigma0_flat,
                          "delta_quadratic": f.delta, "delta_hat0": f.delta_hat0, "n_used": f.n_used})
         report["paper"] = {"per_coupling": rows}
+        # flat-interface sigma_0 against eps for every coupling (mean field: exponent 3/2)
+        flat_rows = []
+        for p in PAPER_PSI:
+            for G in sorted({r.G for r in runs if r.psi == p}):
+                e = G / critical_coupling(p) - 1.0
+                flat_rows.append({"psi": p, "eps": e, "sigma0_flat": coex[G]["sigma0"],
+                                  "n_g": coex[G]["n_g"], "n_l": coex[G]["n_l"]})
+        report["paper"]["flat"] = flat_rows
+        for p in PAPER_PSI:
+            sel = [r for r in flat_rows if r["psi"] == p]
+            A, mu = power_law([r["eps"] for r in sel], [r["sigma0_flat"] for r in sel])
+            report["paper"][f"sigma0_power_law_{p}"] = {"A": A, "mu": mu}
         for p in PAPER_PSI + ("both",):
             sel = [r for r in rows if p == "both" or r["psi"] == p]
             A, lam = power_law([r["eps"] for r in sel], [r["delta"] for r in sel])
