@@ -218,10 +218,14 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int reps, long long* choice);
 /* Select the step kernel's configuration by the code lbm_autotune reports:
  * kind * 10^8 + bx * 10^6 + by * 10^4 + (kind ? z chunk * 10 + prefetch depth : z chunk),
  * kind 0 the register-load kernel, 1 the cp.async-pipelined kernel, 2 the row-bulk
- * pipelined kernel (1 and 2: F32/F64 storage only, z chunk 0 = chosen by the
- * launcher; 2 needs nx % 4 == 0 and nx >= bx + 8).  A code
- * that is not compiled for this context's precision and stencil gives LBM_EINVAL.
- * lbm_get_tile returns the current code.  Results do not depend on the choice. */
+ * pipelined kernel, 4 the pipelined kernel with 16-byte row chunks, 5 the unit-tau
+ * moment kernel (for tau != 1 the same code runs kind 4).  Kinds 1-5: F32/F64
+ * storage only, z chunk 0 = chosen by the launcher; 2, 4 and 5 need nx % 4 == 0
+ * and nx >= bx + 8.  The default (lbm_create) is kind 5 where it applies, else
+ * kind 1 (kind 0 for F16).  A code that is not compiled for this context's
+ * precision, stencil and box gives LBM_EINVAL.  lbm_get_tile returns the current
+ * code.  Results do not depend on the choice: all kinds do the same arithmetic
+ * per node and give bitwise-equal fields. */
 lbm_status lbm_set_tile(lbm_ctx* ctx, long long code);
 lbm_status lbm_get_tile(const lbm_ctx* ctx, long long* code);
 
