@@ -164,9 +164,11 @@ lbm_status lbm_step(lbm_ctx* ctx, long long n);
 /* Sec. IV convergence loop: every check_every steps (the paper uses 2^11) compare
  * Delta P and the velocity field with the previous check; stop when
  * |dP(t) - dP(t - check)| / |dP(t - check)| < tol_dP_rel (paper 1e-5) or
- * delta u < tol_du (paper 1e-12), or after max_steps (LBM_ENOTCONV).  Writes the
- * steps taken and the criterion that fired (0/1/2) when the pointers are non-null.
- * Synchronises once per check. */
+ * delta u < tol_du (paper 1e-12), or after max_steps (LBM_ENOTCONV).  A droplet
+ * or bubble found collapsed (status bit 1) at two checks in a row ends the loop
+ * with LBM_ECOLLAPSE (it cannot come back).  Writes the steps taken and the
+ * criterion that fired (0/1/2) when the pointers are non-null.  Synchronises once
+ * per check. */
 lbm_status lbm_run_to_convergence(lbm_ctx* ctx, long long max_steps, long long check_every,
                                   double tol_dP_rel, double tol_du,
                                   long long* steps_done, int* criterion);
@@ -290,9 +292,11 @@ lbm_status lbm_tolman_fit(const double* R_s, const double* sigma_s, const int* i
  * next run when its lattice finishes (converged, max_steps reached, or a non-finite
  * field); check_every is rounded up to even; *lattice_updates (may be null)
  * receives the lattice updates done.  Synchronises once per check.
+ * A lattice whose droplet or bubble has collapsed (status bit 1) at two checks in
+ * a row is finished early with LBM_ECOLLAPSE: it can no longer give a point.
  * lbm_batch_result: the observables of a finished run (criterion filled in) and
- * its outcome: LBM_OK (converged), LBM_ENOTCONV, LBM_ENUMERIC, LBM_ETIMEOUT, or the
- * error that stopped its set-up. */
+ * its outcome: LBM_OK (converged), LBM_ENOTCONV, LBM_ECOLLAPSE, LBM_ENUMERIC,
+ * LBM_ETIMEOUT, or the error that stopped its set-up. */
 typedef struct lbm_batch lbm_batch;
 size_t lbm_batch_workspace_bytes(int slots, lbm_box max_box, int stencil, int prec);
 lbm_status lbm_batch_create(int slots, lbm_box max_box, int stencil, int prec, void* dev_workspace,

@@ -7,5 +7,5 @@ C ABI of include/lbm.h).  This package is its Python binding.
 """
 from .lbm import *  # noqa: F401,F403
 from .lbm import Batch, Lattice, make_box, make_eos  # noqa: F401
-from ._lib import (EXPORTS, LBM_EINVAL, LBM_ENOTCONV, LBM_ENUMERIC, LBM_ETIMEOUT, LBM_OK,  # noqa: F401
-                   LBMError, lbm_obs)
+from ._lib import (EXPORTS, LBM_ECOLLAPSE, LBM_EINVAL, LBM_ENOTCONV, LBM_ENUMERIC,  # noqa: F401
+                   LBM_ETIMEOUT, LBM_OK, LBMError, lbm_obs)

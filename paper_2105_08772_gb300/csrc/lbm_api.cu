@@ -652,6 +652,7 @@ lbm_status lbm_run_to_convergence(lbm_ctx* c, long long max_steps, long long che
     st = lbm_step(c, k);
     if (st != LBM_OK) return st;
     done += k;
+    const unsigned prev_bits = c->last.status_bits;
     st = lbm_observables(c, nullptr);
     if (st != LBM_OK) return st;
     if (c->last.status_bits & 16u) {
@@ -663,6 +664,12 @@ lbm_status lbm_run_to_convergence(lbm_ctx* c, long long max_steps, long long che
       if (steps_done) *steps_done = done;
       if (criterion) *criterion = 0;
       return fail(c, LBM_ENUMERIC, "non-finite or non-positive density after %lld steps", c->steps);
+    }
+    if ((c->last.status_bits & 2u) && (prev_bits & 2u)) {   // collapsed at two checks in a row
+      if (steps_done) *steps_done = done;
+      if (criterion) *criterion = 0;
+      c->last.criterion = 0;
+      return fail(c, LBM_ECOLLAPSE, "the droplet/bubble collapsed (after %lld steps)", c->steps);
     }
     if (c->last.dP_rel_change < tol_dP_rel) { crit = 1; break; }
     if (c->last.du < tol_du) { crit = 2; break; }
@@ -1429,11 +1436,15 @@ lbm_status lbm_batch_run(lbm_batch* b, long long max_steps, long long check_ever
     for (int k = 0; k < b->slots; ++k) {
       lbm_ctx* c = b->slot_ctx[k];
       if (!c) continue;
+      const unsigned prev_bits = c->last.status_bits;
       c->last = b->obs_host[k];
       c->have_u_old = 1;
       c->have_last = 1;
       if (c->last.status_bits & 16u) batch_finish(b, k, LBM_ETIMEOUT, 0);
       else if (c->last.status_bits & 8u) batch_finish(b, k, LBM_ENUMERIC, 0);
+      // collapsed at two checks in a row: the droplet/bubble is gone for good and the
+      // run can no longer give a point of the sweep; its slot is freed
+      else if ((c->last.status_bits & 2u) && (prev_bits & 2u)) batch_finish(b, k, LBM_ECOLLAPSE, 0);
       else if (c->last.dP_rel_change < tol_dP_rel) batch_finish(b, k, LBM_OK, 1);
       else if (c->last.du < tol_du) batch_finish(b, k, LBM_OK, 2);
       else if (c->steps >= max_steps) batch_finish(b, k, LBM_ENOTCONV, 0);

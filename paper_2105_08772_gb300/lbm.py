@@ -77,12 +77,13 @@ def lbm_step(ctx, n: int):
 
 
 def lbm_run_to_convergence(ctx, max_steps=50_000, check_every=2048, tol_dP_rel=1e-5, tol_du=1e-12):
-    """Returns (status, steps_done, criterion); LBM_ENOTCONV is returned, not raised."""
+    """Returns (status, steps_done, criterion); LBM_ENOTCONV and LBM_ECOLLAPSE are
+    returned, not raised."""
     steps = C.c_longlong(0)
     crit = C.c_int(0)
     st = _lib_.lbm_run_to_convergence(ctx, int(max_steps), int(check_every), float(tol_dP_rel),
                                       float(tol_du), C.byref(steps), C.byref(crit))
-    if st not in (_lib.LBM_OK, _lib.LBM_ENOTCONV):
+    if st not in (_lib.LBM_OK, _lib.LBM_ENOTCONV, _lib.LBM_ECOLLAPSE):
         check(st, ctx)
     return st, steps.value, crit.value
 
