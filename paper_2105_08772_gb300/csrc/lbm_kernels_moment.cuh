@@ -89,8 +89,15 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
   const int xa = x0 - kBulkApron;
 
   // copy positions (as in the chunked kernel)
+  // Thread roles.  When the copy positions and the halo nodes fit in disjoint
+  // whole warps (SPLIT), the first warps copy (one position, all 19 populations)
+  // and the last warps form the halo densities, so no warp carries both extra
+  // loads to the barrier; otherwise two thread groups split the populations of
+  // each position and the halo nodes go to the first threads.
   constexpr int POS = PY * NCH;
-  constexpr int NG = (2 * POS <= NT) ? 2 : 1;
+  constexpr int POSW = (POS + 31) / 32 * 32, NHW = (NH + 31) / 32 * 32;
+  constexpr bool SPLIT = POSW + NHW <= NT;
+  constexpr int NG = SPLIT ? 1 : ((2 * POS <= NT) ? 2 : 1);
   constexpr int NPP = NG == 2 ? 1 : (POS + NT - 1) / NT;
   constexpr int ISPLIT = NG == 2 ? 10 : Q;
   const int grp = NG == 2 ? tid / POS : 0;
@@ -118,9 +125,10 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
   bool validh[NHPER];
 #pragma unroll
   for (int s = 0; s < NHPER; ++s) {
-    const int hh = tid + s * NT;
-    jh[s] = hh < NH ? halo_node<R, PX, PY>(hh) : 0;
-    validh[s] = hh < NH && (jh[s] % PX) < w + 2 * R && (jh[s] / PX) < rows;
+    const int hh = SPLIT ? (s == 0 ? tid - (NT - NHW) : -1) : tid + s * NT;
+    const bool mine = hh >= 0 && hh < NH;
+    jh[s] = mine ? halo_node<R, PX, PY>(hh) : 0;
+    validh[s] = mine && (jh[s] % PX) < w + 2 * R && (jh[s] / PX) < rows;
   }
   const int nplanes = zc + 2 * R;
 
