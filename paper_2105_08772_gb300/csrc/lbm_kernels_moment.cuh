@@ -15,7 +15,8 @@
 // Copies: the 16-byte row chunks of the chunked kernel (lbm_kernels_chunk.cuh).
 // Thread roles in the density pass: each thread forms its own column's padded
 // node (ty + R, tx + R) -- its interior node, whose moments it keeps -- and
-// the NPAD - NT nodes of the halo ring are dealt out to the threads.
+// the NPAD - NT nodes of the halo ring are dealt out to the threads (to warps
+// that do not copy, where the tile allows it).
 // The arithmetic per node is the chunked kernel's (same sums, same collide), so
 // fields are bitwise equal to it.
 #pragma once
@@ -88,7 +89,7 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
   const int rows = h + 2 * R;
   const int xa = x0 - kBulkApron;
 
-  // copy positions (as in the chunked kernel)
+  // Copy positions are the chunked kernel's (one 16-byte chunk of a staged row).
   // Thread roles.  When the copy positions and the halo nodes fit in disjoint
   // whole warps (SPLIT), the first warps copy (one position, all 19 populations)
   // and the last warps form the halo densities, so no warp carries both extra
