@@ -157,28 +157,50 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
     cp_async_commit();
   };
 
-  // moments of the own interior node for the last R + 2 planes: m[0] newest
-  T mdn[R + 2], mjx[R + 2], mjy[R + 2], mjz[R + 2];
+  // moments of the own interior node for the last R + 1 planes: m[0] newest
+  T mdn[R + 1], mjx[R + 1], mjy[R + 1], mjz[R + 1];
 #pragma unroll
-  for (int r = 0; r <= R + 1; ++r) mdn[r] = mjx[r] = mjy[r] = mjz[r] = (T)0;
+  for (int r = 0; r <= R; ++r) mdn[r] = mjx[r] = mjy[r] = mjz[r] = (T)0;
 
   __syncthreads();   // the previous item's readers are done with every stage and psi plane
 #pragma unroll 1
   for (int q = 0; q < D; ++q) issue(q);
 
-  // One barrier per plane.  Iteration qd forms the densities of plane qd and
-  // collides plane qc = qd - 1 - R, whose psi neighbours qc - R .. qc + R = qd - 1
-  // were all formed before this iteration's barrier.  The density pass writes psi
-  // slot qd % (2R + 2), which none of those 2R + 1 planes occupies; the stage it
-  // reads is not the one issue() refills (that held plane qd - 1, read before the
-  // barrier).  One extra iteration collides the last plane.
+  // One barrier per plane.  Iteration qd collides plane qc = qd - 1 - R, whose psi
+  // neighbours qc - R .. qc + R = qd - 1 were all formed before this iteration's
+  // barrier, and then forms the densities of plane qd.  The density pass writes
+  // psi slot qd % (2R + 2), which none of those 2R + 1 planes occupies; the stage
+  // it reads is not the one issue() refills (that held plane qd - 1, read before
+  // the barrier).  The collision goes first so that the warps' shared-memory load
+  // bursts (density pass) and arithmetic (collision) overlap across warps.  One
+  // extra iteration collides the last plane.
 #pragma unroll 1
   for (int qd = 0; qd <= nplanes; ++qd) {
     cp_async_wait<D - 1>();
     __syncthreads();
     issue(qd + D);
+    const int qc = qd - 1 - R;
+    const int k = qc - R;
+    if (k >= 0 && active) {
+      const T* planes[2 * R + 1];
 #pragma unroll
-    for (int r = R + 1; r > 0; --r) {
+      for (int dz = -R; dz <= R; ++dz) planes[dz + R] = ring + ((qc + dz) % NR) * NPAD + j0;
+      T Fx, Fy, Fz;
+      sc_force_pairs<T, ST, PX>(planes, G, Fx, Fy, Fz);
+      const T dn = mdn[R];       // plane qc = qd - 1 - R: R planes before the newest
+      const T n = n0 + dn;
+      const T inv_n = (T)1 / n;
+      const T ux = (mjx[R] + (T)0.5 * Fx) * inv_n;
+      const T uy = (mjy[R] + (T)0.5 * Fy) * inv_n;
+      const T uz = (mjz[R] + (T)0.5 * Fz) * inv_n;
+      T g[Q];     // written, never read, by the unit-tau collision
+      collide<T, true, true>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, (T)1);
+      const long long node = ((long long)(z0 + k) * ny + (y0 + ty)) * nx + (x0 + tx);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) dst[i * plane + node] = (S)g[i];
+    }
+#pragma unroll
+    for (int r = R; r > 0; --r) {
       mdn[r] = mdn[r - 1];
       mjx[r] = mjx[r - 1];
       mjy[r] = mjy[r - 1];
@@ -210,26 +232,6 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
         for (int i = 0; i < Q; ++i) v[i] = row0[i * PY * XW - cx(i)];
         rs[jh[s]] = psi_of<T>(n0 + sum19(v), d.eos);
       }
-    }
-    const int qc = qd - 1 - R;
-    const int k = qc - R;
-    if (k >= 0 && active) {
-      const T* planes[2 * R + 1];
-#pragma unroll
-      for (int dz = -R; dz <= R; ++dz) planes[dz + R] = ring + ((qc + dz) % NR) * NPAD + j0;
-      T Fx, Fy, Fz;
-      sc_force_pairs<T, ST, PX>(planes, G, Fx, Fy, Fz);
-      const T dn = mdn[R + 1];
-      const T n = n0 + dn;
-      const T inv_n = (T)1 / n;
-      const T ux = (mjx[R + 1] + (T)0.5 * Fx) * inv_n;
-      const T uy = (mjy[R + 1] + (T)0.5 * Fy) * inv_n;
-      const T uz = (mjz[R + 1] + (T)0.5 * Fz) * inv_n;
-      T g[Q];     // written, never read, by the unit-tau collision
-      collide<T, true, true>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, (T)1);
-      const long long node = ((long long)(z0 + k) * ny + (y0 + ty)) * nx + (x0 + tx);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) dst[i * plane + node] = (S)g[i];
     }
   }
   cp_async_wait_all();
