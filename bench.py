@@ -367,7 +367,7 @@ def main():
                 "sample": "one 2048-step interval of the 128^3 droplet, FP64 storage and arithmetic",
                 "hbm_gbs": BYTES_PER_LU["f64"] * N * LBM_STEPS_PER_STEP / (ms * 1e-3) / 1e9,
                 "bound": "alu",
-                "evidence": "ncu: FP64 pipe 82% busy, DRAM throughput 6.6% of peak "
+                "evidence": "ncu: FP64 pipe 81% busy, DRAM throughput 6.6% of peak "
                             "(profiles/lattice_moment_f64_128.md)"}
 
     # the same step kernel on a 256^3 lattice (4x the 128^3 working set): the
