@@ -154,12 +154,21 @@ LatticeDesc desc_of(const lbm_ctx* c, int src_buf) {
   return d;
 }
 
-TileCfg default_tile(lbm_box b, int prec, int stencil) {
+TileCfg default_tile(lbm_box b, int prec, int stencil, double tau) {
   TileCfg t;
   t.zchunk = b.nz < 16 ? b.nz : 16;
   t.bx = 32;
   t.by = stencil == 4 ? 8 : 4;
-  if (prec == kF16) return t;   // register-load kernel
+  if (prec == kF16) {
+    // the moment kernel with FP16 staging (E4, tau = 1, nx % 8 == 0, nx >= 48),
+    // else the register-load kernel
+    if (stencil == 4 && tau == 1.0 && b.nx % 8 == 0 && b.nx >= 48) {
+      t.kind = 5;
+      t.zchunk = 0;
+      t.depth = 2;
+    }
+    return t;
+  }
   const int R = stencil == 4 ? 1 : 2;
   // the moment kernel (tau = 1; the chunked kernel otherwise) when the rows split
   // into 16-byte chunks: 32 x 8 tiles for E4 (prefetch depth 2 from 4M nodes on in
@@ -209,6 +218,16 @@ std::vector<TileCfg> step_candidates(const lbm_ctx* c) {
       TileCfg t{shapes[k][0], shapes[k][1], zc < c->box.nz ? zc : c->box.nz};
       out.push_back(t);
     }
+  if (c->prec == kF16 && c->stencil == 4 && c->tau == 1.0 && c->box.nx % 8 == 0 && c->box.nx >= 48) {
+    for (int depth : {1, 2})
+      for (int zc : {0, 8, 16, 32}) {
+        if (zc > c->box.nz) continue;
+        TileCfg t{32, 8, zc};
+        t.kind = 5;
+        t.depth = depth;
+        out.push_back(t);
+      }
+  }
   if (c->prec != kF16) {
     const int R = radius_of(c->stencil);
     const int (*bs)[3] = c->stencil == 4 ? kBulkE4 : kBulkWide;
@@ -477,7 +496,7 @@ lbm_status lbm_create(lbm_box box, double tau, double G, lbm_eos eos, int stenci
   c->cur = 0;
   c->n0 = 0.0;
   c->scale = 1.0;
-  c->step_cfg = default_tile(box, prec, stencil);
+  c->step_cfg = default_tile(box, prec, stencil, tau);
   c->obs_zchunk = default_obs_zchunk(box);
   c->graph[0] = c->graph[1] = nullptr;
   c->graph_len = 128;

@@ -12,7 +12,9 @@
 // one spare psi plane lets a plane's densities and an earlier plane's collision
 // share one barrier.
 //
-// Copies: the 16-byte row chunks of the chunked kernel (lbm_kernels_chunk.cuh).
+// Copies: the 16-byte row chunks of the chunked kernel (lbm_kernels_chunk.cuh),
+// staged in the storage type (FP16 storage: half the shared memory, a 16-byte
+// chunk is 8 values, so the apron is 8 and nx % 8 == 0 is needed).
 // Thread roles in the density pass: each thread forms its own column's padded
 // node (ty + R, tx + R) -- its interior node, whose moments it keeps -- and
 // the NPAD - NT nodes of the halo ring are dealt out to the threads (to warps
@@ -35,15 +37,26 @@ struct MomentShape {
   static constexpr int NT = BX * BY;
   static constexpr int NH = NPAD - NT;                 // halo ring nodes
   static constexpr int NHPER = (NH + NT - 1) / NT;     // halo nodes per thread
-  static constexpr int XW = BX + 2 * kBulkApron;
-  static constexpr int VE = 16 / (int)sizeof(T);
+  using S = typename Storage<P>::S;                    // stored (and staged) type
+  static constexpr int VE = 16 / (int)sizeof(S);       // elements per 16-byte chunk
+  static constexpr int APRON = VE > kBulkApron ? VE : kBulkApron;   // staged left of the tile
+  static constexpr int XW = BX + 2 * APRON;
   static constexpr int NCH = XW / VE;
   static constexpr int NS = 1 + D;
   static constexpr int NR = 2 * R + 2;                 // psi planes (one spare: one barrier per plane)
   static constexpr size_t stage_elems = (size_t)Q * PY * XW;
-  static constexpr size_t smem_bytes = sizeof(T) * (NS * stage_elems + NR * NPAD);
-  static_assert(R + 1 <= kBulkApron, "apron must cover the pull of the halo");
+  static constexpr size_t smem_bytes = sizeof(S) * NS * stage_elems + sizeof(T) * NR * NPAD;
+  static_assert(R + 1 <= APRON, "apron must cover the pull of the halo");
+  static_assert((sizeof(S) * NS * stage_elems) % 16 == 0, "psi ring stays aligned");
 };
+
+// a staged (stored) value as an arithmetic value: FP16 storage is scaled by 2^k
+template <int P>
+__device__ __forceinline__ typename Storage<P>::T staged_value(typename Storage<P>::S x,
+                                                              typename Storage<P>::T inv_scale) {
+  if constexpr (P == kF16) return __half2float(x) * inv_scale;
+  else return x;
+}
 
 // padded index of the h-th node of the halo ring: R full rows on top, R on the
 // bottom, then R columns on each side of the BY middle rows
@@ -63,12 +76,12 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
   using Sh = MomentShape<P, ST, BX, BY, D>;
   using T = typename Sh::T;
   using S = typename Storage<P>::S;
-  static_assert(sizeof(S) == sizeof(T), "copies move stored values unchanged");
+  constexpr int APRON = Sh::APRON;
   constexpr int R = Sh::R, PX = Sh::PX, PY = Sh::PY, NPAD = Sh::NPAD, NT = Sh::NT, NH = Sh::NH;
   constexpr int NHPER = Sh::NHPER;
   constexpr int XW = Sh::XW, VE = Sh::VE, NCH = Sh::NCH, NS = Sh::NS, NR = Sh::NR;
-  T* stages = reinterpret_cast<T*>(smem_raw);
-  T* ring = stages + NS * Sh::stage_elems;
+  S* stages = reinterpret_cast<S*>(smem_raw);
+  T* ring = reinterpret_cast<T*>(stages + NS * Sh::stage_elems);
 
   const int nx = d.nx, ny = d.ny, nz = d.nz;
   const long long plane = d.plane;
@@ -87,7 +100,8 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
   const int w = min(BX, nx - x0), h = min(BY, ny - y0);
   const bool active = tx < w && ty < h;
   const int rows = h + 2 * R;
-  const int xa = x0 - kBulkApron;
+  const int xa = x0 - APRON;
+  const T inv_scale = (T)(1.0 / d.scale), scale = (T)d.scale;
 
   // Copy positions are the chunked kernel's (one 16-byte chunk of a staged row).
   // Thread roles.  When the copy positions and the halo nodes fit in disjoint
@@ -137,7 +151,7 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
     if (q < nplanes) {
       const int z = wrap(z0 - R + q, nz);
       const int zo[3] = {wrap(z + 1, nz) * ny * nx, z * ny * nx, wrap(z - 1, nz) * ny * nx};
-      T* st = stages + (q % NS) * Sh::stage_elems;
+      S* st = stages + (q % NS) * Sh::stage_elems;
 #pragma unroll
       for (int pp = 0; pp < NPP; ++pp) {
         if (!pok[pp]) continue;
@@ -197,7 +211,7 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
       collide<T, true, true>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, (T)1);
       const long long node = ((long long)(z0 + k) * ny + (y0 + ty)) * nx + (x0 + tx);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) dst[i * plane + node] = (S)g[i];
+      for (int i = 0; i < Q; ++i) Storage<P>::store(dst + i * plane + node, g[i], scale);
     }
 #pragma unroll
     for (int r = R; r > 0; --r) {
@@ -207,13 +221,13 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
       mjz[r] = mjz[r - 1];
     }
     if (qd < nplanes) {  // densities, psi and own moments of plane qd
-      const T* st = stages + (qd % NS) * Sh::stage_elems;
+      const S* st = stages + (qd % NS) * Sh::stage_elems;
       T* rs = ring + (qd % NR) * NPAD;
       if (valid0) {
-        const T* row0 = st + (ty + R) * XW + tx + kBulkApron;
+        const S* row0 = st + (ty + R) * XW + tx + APRON;
         T v[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) v[i] = row0[i * PY * XW - cx(i)];
+        for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XW - cx(i)], inv_scale);
         T dn, jx, jy, jz;
         moments(v, dn, jx, jy, jz);
         rs[j0] = psi_of<T>(n0 + dn, d.eos);
@@ -226,10 +240,10 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
       for (int s = 0; s < NHPER; ++s) {
         if (!validh[s]) continue;
         const int hx = jh[s] % PX, hy = jh[s] / PX;
-        const T* row0 = st + hy * XW + hx + kBulkApron - R;
+        const S* row0 = st + hy * XW + hx + APRON - R;
         T v[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) v[i] = row0[i * PY * XW - cx(i)];
+        for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XW - cx(i)], inv_scale);
         rs[jh[s]] = psi_of<T>(n0 + sum19(v), d.eos);
       }
     }

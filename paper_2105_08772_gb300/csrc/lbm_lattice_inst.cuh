@@ -137,17 +137,22 @@ static cudaError_t launch_chunk(const LatticeDesc& d, int zchunk, bool prepare, 
 template <int P, int ST, int BX, int BY, int D>
 static cudaError_t launch_moment(const LatticeDesc& d, int zchunk, bool prepare, cudaStream_t s) {
   using Sh = MomentShape<P, ST, BX, BY, D>;
-  static_assert(Sh::smem_bytes == moment_smem_bytes(sizeof(typename Sh::T), Sh::R, BX, BY, D),
+  static_assert(Sh::smem_bytes == moment_smem_bytes(sizeof(typename Sh::S), sizeof(typename Sh::T),
+                                                    Sh::R, BX, BY, D),
                 "host and device disagree on the moment kernel's shared memory");
   auto kern = lattice_moment_kernel<P, ST, BX, BY, D>;
   static int resident = 0;
   if (prepare || resident == 0) {
     cudaError_t e = prepare_persistent(kern, Sh::NT, Sh::smem_bytes, &resident);
-    if (e == cudaSuccess && prepare) e = launch_chunk<P, ST, BX, BY, D>(d, 0, true, s);
+    if constexpr (P != kF16)   // the tau != 1 fallback (FP16 storage has none: tau = 1 only)
+      if (e == cudaSuccess && prepare) e = launch_chunk<P, ST, BX, BY, D>(d, 0, true, s);
     if (e != cudaSuccess || prepare) return e;
   }
-  if (d.omega != 1.0) return launch_chunk<P, ST, BX, BY, D>(d, zchunk, false, s);
-  if (d.nx % 4 != 0 || d.nx < BX + 8) return cudaErrorInvalidValue;
+  if (d.omega != 1.0) {
+    if constexpr (P == kF16) return cudaErrorInvalidValue;
+    else return launch_chunk<P, ST, BX, BY, D>(d, zchunk, false, s);
+  }
+  if (d.nx % Sh::VE != 0 || d.nx < BX + 2 * Sh::APRON) return cudaErrorInvalidValue;
   const long long cols = (long long)((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
   const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
   const long long items = cols * ((d.nz + zc - 1) / zc);
@@ -158,7 +163,11 @@ static cudaError_t launch_moment(const LatticeDesc& d, int zchunk, bool prepare,
 
 template <int P, int ST>
 static cudaError_t dispatch_moment(const LatticeDesc& d, TileCfg c, cudaStream_t s) {
-  if constexpr (P == kF16) {
+  if constexpr (P == kF16) {   // FP16 storage: E4, 32 x 8 tiles
+    if (ST == 4 && c.bx == 32 && c.by == 8 && c.depth == 1)
+      return launch_moment<P, 4, 32, 8, 1>(d, c.zchunk, c.prepare, s);
+    if (ST == 4 && c.bx == 32 && c.by == 8 && c.depth == 2)
+      return launch_moment<P, 4, 32, 8, 2>(d, c.zchunk, c.prepare, s);
     return cudaErrorInvalidValue;
   } else {
     const bool prep = c.prepare;

@@ -86,11 +86,14 @@ constexpr int kChunkE4[kNumChunkE4][3] = {{32, 8, 1}, {32, 8, 2}, {32, 4, 1}, {3
 constexpr int kNumChunkWide = 1;
 constexpr int kChunkWide[kNumChunkWide][3] = {{32, 4, 1}};
 
-// dynamic shared memory of the unit-tau moment kernel: 1 + depth stages, psi ring
-// of 2R + 2 padded planes
-constexpr size_t moment_smem_bytes(size_t elem, int R, int bx, int by, int depth) {
-  return elem * ((size_t)(1 + depth) * Q * (by + 2 * R) * (bx + 8) +
-                 (size_t)(2 * R + 2) * (bx + 2 * R) * (by + 2 * R));
+// staged left of a tile by the chunked copies: one 16-byte chunk, at least 4
+constexpr int chunk_apron(size_t stored) { return 16 / (int)stored > 4 ? 16 / (int)stored : 4; }
+// dynamic shared memory of the unit-tau moment kernel: 1 + depth stages of the
+// stored type (rows of bx + 2 apron), psi ring of 2R + 2 padded planes in the
+// arithmetic type
+constexpr size_t moment_smem_bytes(size_t stored, size_t arith, int R, int bx, int by, int depth) {
+  return stored * (size_t)(1 + depth) * Q * (by + 2 * R) * (bx + 2 * chunk_apron(stored)) +
+         arith * (size_t)(2 * R + 2) * (bx + 2 * R) * (by + 2 * R);
 }
 // (bx, by, depth) compiled for the moment kernel (kind 5; tau = 1, else the
 // chunked kernel of the same shape runs)

@@ -385,3 +385,33 @@ def test_moment_kernel_wide_stencils(stencil):
     a.step(40)
     ref = lbm3d.run(f0, oracle_model(stencil=stencil), 40)
     assert np.max(np.abs(a.get_populations() - ref)) < 1e-12
+
+
+@pytest.fixture(scope="module")
+def droplet_state_48():
+    """The droplet workload in a box wide enough for the FP16 moment kernel (nx = 48)."""
+    shape, c = (16, 24, 48), (24, 12, 8)
+    n = lbm3d.drop_density(shape, c, 6.0, 1.8883, 0.1193)
+    f0 = lbm3d.init_from_density(n)
+    return shape, c, f0, lbm3d.run(f0, oracle_model(), 1000)
+
+
+def test_f16_moment_kernel_parity(droplet_state_48):
+    """FP16 storage through the moment kernel (its default at tau = 1, nx % 8 == 0):
+    within the FP16 bound of the oracle (1e-2 after 1000 steps), and as close to the
+    register-load FP16 kernel."""
+    shape, c, f0, ref = droplet_state_48
+    a = lattice(shape, prec="f16")
+    assert a.get_tile() // 100000000 == 5
+    a.init_drop(c, 6.0, 1.8883, 0.1193, 1.0)
+    a.step(1000)
+    b = lattice(shape, prec="f16")
+    b.set_tile(32080016)                  # register-load kernel, 32 x 8, z chunk 16
+    b.init_drop(c, 6.0, 1.8883, 0.1193, 1.0)
+    b.step(1000)
+    rho_ref = lbm3d.density(ref)
+    ra, rb = a.rho(), b.rho()
+    rel = np.max(np.abs(ra - rho_ref) / rho_ref)
+    ab = np.max(np.abs(ra - rb) / rho_ref)
+    print(f"f16 moment kernel: max relative density error {rel:.3e}; vs register-load kernel {ab:.3e}")
+    assert np.isfinite(rel) and rel < 1e-2 and ab < 1e-2
