@@ -267,6 +267,28 @@ lbm_status lbm_flat_interface(double tau, double G, lbm_eos eos, int stencil, in
                               void* dev_workspace, size_t bytes, void* cuda_stream, double* n_g,
                               double* n_l, double* sigma0, long long* steps);
 
+/* ---------------------------------------------------------------- groups of lattices */
+
+/* Step several existing lattices together: one launch of the step kernel per time
+ * step covers all of them (the batch kernel over a table of the contexts), so
+ * small lattices fill the GPU as one larger one does.  The paper has no
+ * counterpart; its runs are independent lattices, which is what makes this
+ * possible.  All contexts need the same stencil and F64 or F32 storage; each
+ * keeps its own box, tau, G and psi and evolves bitwise as under lbm_step.
+ * lbm_group_workspace_bytes: device bytes for the table of n contexts;
+ * lbm_group_create: caller-owned workspace (256-byte aligned), the stream all
+ * group work is enqueued on (order it with the contexts' streams; using the same
+ * stream does), the contexts stay owned by the caller and must outlive the group.
+ * lbm_group_step: advance every lattice n >= 0 steps (async; CUDA graphs of 128
+ * steps); afterwards lbm_observables etc. work per context as usual. */
+typedef struct lbm_group lbm_group;
+size_t lbm_group_workspace_bytes(int n);
+lbm_status lbm_group_create(lbm_ctx* const* ctxs, int n, void* dev_workspace, size_t bytes,
+                            void* cuda_stream, lbm_group** out);
+lbm_status lbm_group_step(lbm_group* g, long long n);
+const char* lbm_group_last_error(const lbm_group* g);
+void lbm_group_destroy(lbm_group* g);
+
 /* ---------------------------------------------------------------- Tolman fit */
 
 /* Least-squares fit of Eq. (2) / Eq. (12): sigma_s = sigma0 (1 - 2 delta x + c x^2)

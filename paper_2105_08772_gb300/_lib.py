@@ -31,7 +31,8 @@ EXPORTS = (
     "lbm_storage_params", "lbm_density_moments_noalloc", "lbm_batch_workspace_bytes",
     "lbm_batch_create", "lbm_batch_enqueue", "lbm_batch_run", "lbm_batch_result",
     "lbm_batch_last_error", "lbm_batch_destroy", "lbm_pn_profile", "lbm_flat_workspace_bytes",
-    "lbm_flat_interface", "lbm_coexistence_estimate",
+    "lbm_flat_interface", "lbm_coexistence_estimate", "lbm_group_workspace_bytes", "lbm_group_create",
+    "lbm_group_step", "lbm_group_last_error", "lbm_group_destroy",
     "lbm_strerror", "lbm_last_error", "lbm_tolman_fit",
 )
 
@@ -110,6 +111,11 @@ def _load():
         "lbm_pn_profile": (C.c_int, [_P, _D, C.c_longlong]),
         "lbm_flat_workspace_bytes": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
         "lbm_coexistence_estimate": (C.c_int, [lbm_eos, C.c_double, _D, _D, _D]),
+        "lbm_group_workspace_bytes": (C.c_size_t, [C.c_int]),
+        "lbm_group_create": (C.c_int, [C.POINTER(_P), C.c_int, _P, C.c_size_t, _P, C.POINTER(_P)]),
+        "lbm_group_step": (C.c_int, [_P, C.c_longlong]),
+        "lbm_group_last_error": (C.c_char_p, [_P]),
+        "lbm_group_destroy": (None, [_P]),
         "lbm_flat_interface": (C.c_int, [C.c_double, C.c_double, lbm_eos, C.c_int, C.c_int, C.c_int,
                                          C.c_double, C.c_double, C.c_longlong, C.c_double, _P,
                                          C.c_size_t, _P, _D, _D, _D, C.POINTER(C.c_longlong)]),

@@ -1487,3 +1487,194 @@ lbm_status lbm_batch_result(const lbm_batch* b, int id, lbm_obs* out) {
 const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : g_err; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- groups of lattices
+
+struct lbm_group {
+  std::vector<lbm_ctx*> ctx;
+  int stencil, prec, mode;
+  cudaStream_t stream;
+  cudaStream_t cap_stream;
+  BatchEntry* table_dev;
+  BatchHeader* hdr_dev;
+  std::vector<BatchEntry> table_host;
+  BatchHeader hdr_host{};
+  int grid = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 128;        // even: a replay keeps every lattice's parity
+  char err[512];
+};
+
+namespace {
+
+lbm_status gfail(lbm_group* g, lbm_status s, const char* fmt, ...) {
+  char* buf = g ? g->err : g_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define LBM_GCUDA(g, call)                                                               \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return gfail((g), LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+// the table of the group's lattices with their current parities; one z chunk for
+// all of them, chosen like the single-lattice launcher (fewest rounds x planes)
+lbm_status group_upload(lbm_group* g) {
+  const TileCfg t = batch_tile(g->prec, g->stencil, g->mode);
+  const int R = radius_of(g->stencil);
+  int max_nz = 1;
+  for (lbm_ctx* c : g->ctx) max_nz = c->box.nz > max_nz ? c->box.nz : max_nz;
+  int best_zc = max_nz;
+  long long best_cost = -1;
+  for (int zc = 1; zc <= max_nz; ++zc) {
+    long long items = 0;
+    for (lbm_ctx* c : g->ctx)
+      items += (long long)((c->box.nx + t.bx - 1) / t.bx) * ((c->box.ny + t.by - 1) / t.by) *
+               ((c->box.nz + zc - 1) / zc);
+    const long long rounds = (items + g->grid - 1) / g->grid;
+    const long long cost = rounds * (zc + 2 * R);
+    if (best_cost < 0 || cost <= best_cost) {
+      best_cost = cost;
+      best_zc = zc;
+    }
+  }
+  g->table_host.clear();
+  long long items = 0;
+  for (lbm_ctx* c : g->ctx) {
+    BatchEntry e;
+    e.d = desc_of(c, 0);
+    e.parity = c->cur;
+    e.zchunk = best_zc < c->box.nz ? best_zc : c->box.nz;
+    e.item_begin = items;
+    items += (long long)((c->box.nx + t.bx - 1) / t.bx) * ((c->box.ny + t.by - 1) / t.by) *
+             ((c->box.nz + e.zchunk - 1) / e.zchunk);
+    g->table_host.push_back(e);
+  }
+  g->hdr_host.n = (int)g->table_host.size();
+  g->hdr_host.total_items = items;
+  LBM_GCUDA(g, cudaMemcpyAsync(g->table_dev, g->table_host.data(), sizeof(BatchEntry) * g->table_host.size(),
+                               cudaMemcpyHostToDevice, g->stream));
+  LBM_GCUDA(g, cudaMemcpyAsync(g->hdr_dev, &g->hdr_host, sizeof(BatchHeader), cudaMemcpyHostToDevice, g->stream));
+  LBM_GCUDA(g, cudaStreamSynchronize(g->stream));   // the host copy is reused
+  return LBM_OK;
+}
+
+}  // namespace
+
+size_t lbm_group_workspace_bytes(int n) {
+  if (n < 1) return 0;
+  return align256(sizeof(BatchEntry) * (size_t)n) + align256(sizeof(BatchHeader));
+}
+
+lbm_status lbm_group_create(lbm_ctx* const* ctxs, int n, void* dev_workspace, size_t bytes,
+                            void* cuda_stream, lbm_group** out) {
+  if (!out) return gfail(nullptr, LBM_EINVAL, "out is null");
+  *out = nullptr;
+  if (!ctxs || n < 1) return gfail(nullptr, LBM_EINVAL, "need n >= 1 contexts");
+  if (!dev_workspace || ((uintptr_t)dev_workspace & 255) != 0)
+    return gfail(nullptr, LBM_EINVAL, "workspace null or not 256-byte aligned");
+  if (bytes < lbm_group_workspace_bytes(n))
+    return gfail(nullptr, LBM_ENOMEM, "workspace has %zu bytes, needs %zu", bytes, lbm_group_workspace_bytes(n));
+  for (int k = 0; k < n; ++k) {
+    if (!ctxs[k]) return gfail(nullptr, LBM_EINVAL, "context %d is null", k);
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return gfail(nullptr, LBM_EINVAL, "context %d appears twice", k);
+    if (ctxs[k]->prec != ctxs[0]->prec || ctxs[k]->stencil != ctxs[0]->stencil)
+      return gfail(nullptr, LBM_EINVAL, "all contexts need the same storage and stencil");
+  }
+  if (ctxs[0]->prec == kF16) return gfail(nullptr, LBM_EINVAL, "groups need F64 or F32 storage");
+  lbm_group* g = new lbm_group();
+  g->err[0] = 0;
+  g->ctx.assign(ctxs, ctxs + n);
+  g->stencil = ctxs[0]->stencil;
+  g->prec = ctxs[0]->prec;
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  char* ws = static_cast<char*>(dev_workspace);
+  g->table_dev = reinterpret_cast<BatchEntry*>(ws);
+  g->hdr_dev = reinterpret_cast<BatchHeader*>(ws + align256(sizeof(BatchEntry) * (size_t)n));
+  // kernel mode as for a batch: the moment kernel when every lattice allows it
+  bool unit = true, moment = true;
+  const int bx = batch_tile(g->prec, g->stencil, kBatchMoment).bx;
+  for (lbm_ctx* c : g->ctx) {
+    if (c->tau != 1.0) unit = false;
+    if (c->box.nx % 4 != 0 || c->box.nx < bx + 8) moment = false;
+  }
+  g->mode = !unit ? kBatchMixedTau : (moment ? kBatchMoment : kBatchUnitTau);
+  cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess)
+    e = launch_batch(g->prec, g->stencil, g->mode, g->table_dev, g->hdr_dev, 0, true, &g->grid, g->stream);
+  if (e != cudaSuccess) {
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    delete g;
+    return gfail(nullptr, LBM_ECUDA, "group set-up failed: %s", cudaGetErrorString(e));
+  }
+  *out = g;
+  return LBM_OK;
+}
+
+void lbm_group_destroy(lbm_group* g) {
+  if (!g) return;
+  if (g->graph) cudaGraphExecDestroy(g->graph);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+  delete g;
+}
+
+lbm_status lbm_group_step(lbm_group* g, long long n) {
+  if (!g) return gfail(nullptr, LBM_EINVAL, "null group");
+  if (n < 0) return gfail(g, LBM_EINVAL, "n must be >= 0");
+  for (lbm_ctx* c : g->ctx)
+    if (!c->initialised) return gfail(g, LBM_EINVAL, "a lattice of the group is not initialised");
+  if (n == 0) return LBM_OK;
+  // the table holds each lattice's buffer parity: write it again (and drop the
+  // graph captured with the old table) when any lattice's parity has changed, e.g.
+  // after an odd number of steps or a lattice stepped on its own
+  bool stale = g->table_host.size() != g->ctx.size();
+  for (size_t k = 0; !stale && k < g->ctx.size(); ++k) stale = g->table_host[k].parity != g->ctx[k]->cur;
+  if (stale) {
+    lbm_status st = group_upload(g);
+    if (st != LBM_OK) return st;
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    g->graph = nullptr;
+  }
+  if (n >= g->graph_len && !g->graph) {
+    cudaGraph_t gr = nullptr;
+    LBM_GCUDA(g, cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < g->graph_len && e == cudaSuccess; ++k)
+      e = launch_batch(g->prec, g->stencil, g->mode, g->table_dev, g->hdr_dev, k & 1, false, nullptr,
+                       g->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &gr);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (gr) cudaGraphDestroy(gr);
+      return gfail(g, LBM_ECUDA, "group graph capture failed: %s",
+                   cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&g->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      g->graph = nullptr;
+      return gfail(g, LBM_ECUDA, "group graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+  }
+  long long done = 0;
+  while (n - done >= g->graph_len) {
+    LBM_GCUDA(g, cudaGraphLaunch(g->graph, g->stream));
+    done += g->graph_len;
+  }
+  for (long long k = 0; done + k < n; ++k)
+    LBM_GCUDA(g, launch_batch(g->prec, g->stencil, g->mode, g->table_dev, g->hdr_dev, (int)(k & 1), false,
+                              nullptr, g->stream));
+  for (lbm_ctx* c : g->ctx) {
+    c->steps += n;
+    c->cur ^= (int)(n & 1);
+  }
+  return LBM_OK;
+}
+
+const char* lbm_group_last_error(const lbm_group* g) { return g ? g->err : g_err; }

@@ -311,6 +311,61 @@ class Batch:
             pass
 
 
+def _gcheck(status: int, g) -> int:
+    if status != _lib.LBM_OK:
+        raise LBMError(status, _lib_.lbm_group_last_error(g).decode())
+    return status
+
+
+def lbm_group_workspace_bytes(n: int) -> int:
+    return int(_lib_.lbm_group_workspace_bytes(int(n)))
+
+
+def lbm_group_create(ctxs, dev_workspace: int, nbytes: int, stream: int):
+    arr = (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    out = C.c_void_p()
+    _gcheck(_lib_.lbm_group_create(arr, len(ctxs), C.c_void_p(dev_workspace), C.c_size_t(nbytes),
+                                   C.c_void_p(stream), C.byref(out)), None)
+    return out
+
+
+def lbm_group_step(g, n: int):
+    _gcheck(_lib_.lbm_group_step(g, int(n)), g)
+
+
+def lbm_group_destroy(g) -> None:
+    _lib_.lbm_group_destroy(g)
+
+
+class Group:
+    """Several Lattice objects stepped together, one launch per time step (see
+    lbm_group_* in include/lbm.h).  The lattices must outlive the group."""
+
+    def __init__(self, lattices, stream=None):
+        import torch
+        self.lattices = list(lattices)
+        self.nbytes = lbm_group_workspace_bytes(len(self.lattices))
+        self.workspace = torch.empty(self.nbytes + 256, dtype=torch.uint8, device="cuda")
+        ptr = self.workspace.data_ptr()
+        ptr += (-ptr) % 256
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.g = lbm_group_create([lat.ctx for lat in self.lattices], ptr, self.nbytes, s.cuda_stream)
+
+    def step(self, n: int):
+        lbm_group_step(self.g, n)
+
+    def close(self):
+        if getattr(self, "g", None) is not None:
+            lbm_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------- convenience object
 
 @dataclass
