@@ -187,6 +187,20 @@ TileCfg default_tile(lbm_box b, int prec, int stencil, double tau) {
       return t;
     }
   }
+  // odd or narrow rows: the moment kernel with element copies (tau = 1; the
+  // pipelined kernel otherwise) where two CTAs of it fit an SM
+  {
+    const int by = stencil == 4 ? 8 : 4;
+    const size_t el = prec == kF64 ? 8 : 4;
+    if (moment_elem_two_per_sm(el, R, 32, by, 1) && async_smem_bytes(el, R, 32, by, 1) <= kMaxSmemPerCta) {
+      t.kind = 6;
+      t.bx = 32;
+      t.by = by;
+      t.zchunk = 0;
+      t.depth = 1;
+      return t;
+    }
+  }
   // pipelined kernel with a launcher-chosen z chunk, if one compiled shape fits
   const int by_pref[2] = {(prec == kF64 || stencil != 4) ? 4 : 8, 4};
   for (int by : by_pref) {
@@ -243,6 +257,21 @@ std::vector<TileCfg> step_candidates(const lbm_ctx* c) {
         t.kind = 2;
         t.depth = bs[k][2];
         out.push_back(t);
+      }
+    }
+    {  // kind 6: the moment kernel with element copies (any nx), 2 CTAs per SM
+      const int es[3][3] = {{32, 8, 1}, {32, 8, 2}, {32, 4, 1}};
+      for (const auto& e : es) {
+        if ((c->stencil == 4) != (e[1] == 8)) continue;
+        if (async_smem_bytes(storage_bytes(c->prec), R, e[0], e[1], e[2]) > kMaxSmemPerCta) continue;
+        if (!moment_elem_two_per_sm(storage_bytes(c->prec), R, e[0], e[1], e[2])) continue;
+        for (int zc : {0, 8, 16, 32}) {
+          if (zc > c->box.nz) continue;
+          TileCfg t{e[0], e[1], zc};
+          t.kind = 6;
+          t.depth = e[2];
+          out.push_back(t);
+        }
       }
     }
     const int (*ms)[3] = c->stencil == 4 ? kMomentE4 : kMomentWide;
@@ -1245,7 +1274,7 @@ int batch_mode(const lbm_batch* b) {
     if (r.tau != 1.0) unit = false;
     if (r.box.nx % 4 != 0 || r.box.nx < bx + 8) moment = false;
   }
-  return !unit ? kBatchMixedTau : (moment ? kBatchMoment : kBatchUnitTau);
+  return !unit ? kBatchMixedTau : (moment ? kBatchMoment : kBatchMomentElem);
 }
 
 lbm_status batch_fill(lbm_batch* b) {
@@ -1605,7 +1634,7 @@ lbm_status lbm_group_create(lbm_ctx* const* ctxs, int n, void* dev_workspace, si
     if (c->tau != 1.0) unit = false;
     if (c->box.nx % 4 != 0 || c->box.nx < bx + 8) moment = false;
   }
-  g->mode = !unit ? kBatchMixedTau : (moment ? kBatchMoment : kBatchUnitTau);
+  g->mode = !unit ? kBatchMixedTau : (moment ? kBatchMoment : kBatchMomentElem);
   cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess)
     e = launch_batch(g->prec, g->stencil, g->mode, g->table_dev, g->hdr_dev, 0, true, &g->grid, g->stream);

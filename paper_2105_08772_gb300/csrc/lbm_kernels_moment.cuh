@@ -27,7 +27,7 @@
 
 namespace lbm {
 
-template <int P, int ST, int BX, int BY, int D>
+template <int P, int ST, int BX, int BY, int D, bool ELEM = false>
 struct MomentShape {
   using T = typename Storage<P>::T;
   static constexpr int R = stencil_radius<ST>();
@@ -44,8 +44,14 @@ struct MomentShape {
   static constexpr int NCH = XW / VE;
   static constexpr int NS = 1 + D;
   static constexpr int NR = 2 * R + 2;                 // psi planes (one spare: one barrier per plane)
-  static constexpr size_t stage_elems = (size_t)Q * PY * XW;
+  static constexpr int NPER = (NPAD + NT - 1) / NT;   // padded nodes a thread copies (ELEM)
+  // ELEM: stage[i][j] holds population i pulled to padded node j (4- or 8-byte
+  // element copies, any nx); else staged rows of XW values (16-byte chunks)
+  static constexpr size_t stage_elems = ELEM ? (size_t)Q * NPAD : (size_t)Q * PY * XW;
   static constexpr size_t smem_bytes = sizeof(S) * NS * stage_elems + sizeof(T) * NR * NPAD;
+  // ELEM variants run 2 CTAs per SM: the element copies go through L1, which
+  // needs the capacity that more CTAs' shared memory would take
+  static constexpr int MIN_BLOCKS = ELEM ? 2 : async_min_blocks<NT, smem_bytes>();
   static_assert(R + 1 <= APRON, "apron must cover the pull of the halo");
   static_assert((sizeof(S) * NS * stage_elems) % 16 == 0, "psi ring stays aligned");
 };
@@ -70,10 +76,10 @@ __device__ __forceinline__ int halo_node(int h) {
   return row * PX + (c < R ? c : PX - 2 * R + c);
 }
 
-template <int P, int ST, int BX, int BY, int D>
+template <int P, int ST, int BX, int BY, int D, bool ELEM = false>
 __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zchunk, long long item,
                                                     unsigned char* smem_raw) {
-  using Sh = MomentShape<P, ST, BX, BY, D>;
+  using Sh = MomentShape<P, ST, BX, BY, D, ELEM>;
   using T = typename Sh::T;
   using S = typename Storage<P>::S;
   constexpr int APRON = Sh::APRON;
@@ -111,7 +117,7 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
   // each position and the halo nodes go to the first threads.
   constexpr int POS = PY * NCH;
   constexpr int POSW = (POS + 31) / 32 * 32, NHW = (NH + 31) / 32 * 32;
-  constexpr bool SPLIT = POSW + NHW <= NT;
+  constexpr bool SPLIT = !ELEM && POSW + NHW <= NT;
   constexpr int NG = SPLIT ? 1 : ((2 * POS <= NT) ? 2 : 1);
   constexpr int NPP = NG == 2 ? 1 : (POS + NT - 1) / NT;
   constexpr int ISPLIT = NG == 2 ? 10 : Q;
@@ -133,6 +139,26 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
     pgx[pp] = wrap(xa + k * VE, nx);
     psm[pp] = jy * XW + k * VE;
   }
+  // ELEM copies (as in the pipelined kernel): padded nodes tid + s NT, their
+  // wrapped source columns and row offsets for c = -1, 0, +1
+  constexpr int NPER = Sh::NPER;
+  int exs[ELEM ? NPER : 1][3], eyr[ELEM ? NPER : 1][3];
+  bool ecv[ELEM ? NPER : 1];
+  if constexpr (ELEM) {
+#pragma unroll
+    for (int s = 0; s < NPER; ++s) {
+      const int j = tid + s * NT;
+      const int jx = j % PX, jy = j / PX;
+      ecv[s] = j < NPAD && jx < w + 2 * R && jy < rows;
+      const int gx = wrap(x0 + jx - R, nx), gy = wrap(y0 + (ecv[s] ? jy : 0) - R, ny);
+      exs[s][0] = wrap(gx + 1, nx);
+      exs[s][1] = gx;
+      exs[s][2] = wrap(gx - 1, nx);
+      eyr[s][0] = wrap(gy + 1, ny) * nx;
+      eyr[s][1] = gy * nx;
+      eyr[s][2] = wrap(gy - 1, ny) * nx;
+    }
+  }
   // density-pass nodes: own column's node (padded (ty + R, tx + R)) and halo ring nodes
   const int j0 = (ty + R) * PX + (tx + R);
   const bool valid0 = tx < w + R && ty < h + R;
@@ -152,6 +178,19 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
       const int z = wrap(z0 - R + q, nz);
       const int zo[3] = {wrap(z + 1, nz) * ny * nx, z * ny * nx, wrap(z - 1, nz) * ny * nx};
       S* st = stages + (q % NS) * Sh::stage_elems;
+      if constexpr (ELEM) {
+#pragma unroll
+        for (int s = 0; s < NPER; ++s) {
+          if (!ecv[s]) continue;
+          const int j = tid + s * NT;
+#pragma unroll
+          for (int i = 0; i < Q; ++i) {
+            const S* gsrc = srcp[i] + (zo[cz(i) + 1] + eyr[s][cy(i) + 1] + exs[s][cx(i) + 1]);
+            if constexpr (sizeof(S) == 8) cp_async_elem8(st + i * NPAD + j, gsrc);
+            else cp_async_elem4(st + i * NPAD + j, gsrc);
+          }
+        }
+      } else {
 #pragma unroll
       for (int pp = 0; pp < NPP; ++pp) {
         if (!pok[pp]) continue;
@@ -166,6 +205,7 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
             cp_async_chunk16(st + i * PY * XW + psm[pp],
                              srcp[i] + (zo[cz(i) + 1] + prow[pp][cy(i) + 1] + pgx[pp]));
         }
+      }
       }
     }
     cp_async_commit();
@@ -224,10 +264,15 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
       const S* st = stages + (qd % NS) * Sh::stage_elems;
       T* rs = ring + (qd % NR) * NPAD;
       if (valid0) {
-        const S* row0 = st + (ty + R) * XW + tx + APRON;
         T v[Q];
+        if constexpr (ELEM) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XW - cx(i)], inv_scale);
+          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(st[i * NPAD + j0], inv_scale);
+        } else {
+          const S* row0 = st + (ty + R) * XW + tx + APRON;
+#pragma unroll
+          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XW - cx(i)], inv_scale);
+        }
         T dn, jx, jy, jz;
         moments(v, dn, jx, jy, jz);
         rs[j0] = psi_of<T>(n0 + dn, d.eos);
@@ -239,11 +284,16 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
 #pragma unroll
       for (int s = 0; s < NHPER; ++s) {
         if (!validh[s]) continue;
-        const int hx = jh[s] % PX, hy = jh[s] / PX;
-        const S* row0 = st + hy * XW + hx + APRON - R;
         T v[Q];
+        if constexpr (ELEM) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XW - cx(i)], inv_scale);
+          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(st[i * NPAD + jh[s]], inv_scale);
+        } else {
+          const int hx = jh[s] % PX, hy = jh[s] / PX;
+          const S* row0 = st + hy * XW + hx + APRON - R;
+#pragma unroll
+          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XW - cx(i)], inv_scale);
+        }
         rs[jh[s]] = psi_of<T>(n0 + sum19(v), d.eos);
       }
     }
@@ -251,21 +301,21 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
   cp_async_wait_all();
 }
 
-template <int P, int ST, int BX, int BY, int D>
-__global__ void __launch_bounds__(BX * BY, (async_min_blocks<BX * BY, MomentShape<P, ST, BX, BY, D>::smem_bytes>()))
+template <int P, int ST, int BX, int BY, int D, bool ELEM = false>
+__global__ void __launch_bounds__(BX * BY, (MomentShape<P, ST, BX, BY, D, ELEM>::MIN_BLOCKS))
 lattice_moment_kernel(LatticeDesc d, int zchunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ncols = ((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
   const long long items = (long long)ncols * ((d.nz + zchunk - 1) / zchunk);
 #pragma unroll 1
   for (long long item = blockIdx.x; item < items; item += gridDim.x)
-    moment_process_item<P, ST, BX, BY, D>(d, zchunk, item, smem_raw);
+    moment_process_item<P, ST, BX, BY, D, ELEM>(d, zchunk, item, smem_raw);
 }
 
 // A batch of tau = 1 lattices (see lattice_async_batch_kernel for the table):
 // every lattice takes the moment kernel's path.
-template <int P, int ST, int BX, int BY, int D>
-__global__ void __launch_bounds__(BX * BY, (async_min_blocks<BX * BY, MomentShape<P, ST, BX, BY, D>::smem_bytes>()))
+template <int P, int ST, int BX, int BY, int D, bool ELEM = false>
+__global__ void __launch_bounds__(BX * BY, (MomentShape<P, ST, BX, BY, D, ELEM>::MIN_BLOCKS))
 lattice_moment_batch_kernel(const BatchEntry* __restrict__ table, const BatchHeader* __restrict__ hdr,
                             int step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -284,7 +334,7 @@ lattice_moment_batch_kernel(const BatchEntry* __restrict__ table, const BatchHea
       d.src = d.dst;
       d.dst = const_cast<void*>(t);
     }
-    moment_process_item<P, ST, BX, BY, D>(d, table[lo].zchunk, item - table[lo].item_begin, smem_raw);
+    moment_process_item<P, ST, BX, BY, D, ELEM>(d, table[lo].zchunk, item - table[lo].item_begin, smem_raw);
   }
 }
 

@@ -227,6 +227,60 @@ static cudaError_t launch_async(const LatticeDesc& d, int zchunk, bool prepare, 
   return launch_async_variant<P, ST, BX, BY, D, false>(d, zchunk, false, s);
 }
 
+// the moment kernel with element copies (kind 6: any nx; tau = 1, else the
+// pipelined kernel of the same shape).  Two CTAs per SM, and the shared-memory
+// carveout set to what they need, so L1 keeps the rest for the element copies.
+template <int P, int ST, int BX, int BY, int D>
+static cudaError_t launch_moment_elem(const LatticeDesc& d, int zchunk, bool prepare, cudaStream_t s) {
+  using Sh = MomentShape<P, ST, BX, BY, D, true>;
+  static_assert(Sh::smem_bytes == moment_elem_smem_bytes(sizeof(typename Sh::S), sizeof(typename Sh::T),
+                                                         Sh::R, BX, BY, D),
+                "host and device disagree on the moment kernel's shared memory");
+  auto kern = lattice_moment_kernel<P, ST, BX, BY, D, true>;
+  static int resident = 0;
+  if (prepare || resident == 0) {
+    cudaError_t e = prepare_persistent(kern, Sh::NT, Sh::smem_bytes, &resident);
+    if (e == cudaSuccess) {
+      static_assert(2 * (Sh::smem_bytes + 1024) <= 228 * 1024, "two CTAs of kind 6 must fit an SM");
+      const int pct = (int)((2 * (Sh::smem_bytes + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+      int per_sm = 0, dev = 0, sms = 0;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::NT, Sh::smem_bytes);
+      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) resident = (per_sm < 2 ? (per_sm > 0 ? per_sm : 1) : 2) * sms;
+    }
+    if (e == cudaSuccess && prepare) e = launch_async<P, ST, BX, BY, D>(d, 0, true, s);
+    if (e != cudaSuccess || prepare) return e;
+  }
+  if (d.omega != 1.0) return launch_async<P, ST, BX, BY, D>(d, zchunk, false, s);
+  const long long cols = (long long)((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
+  const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
+  const long long items = cols * ((d.nz + zc - 1) / zc);
+  const long long grid = items < resident ? items : resident;
+  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, zc);
+  return cudaGetLastError();
+}
+
+template <int P, int ST>
+static cudaError_t dispatch_moment_elem(const LatticeDesc& d, TileCfg c, cudaStream_t s) {
+  if constexpr (P == kF16) {
+    return cudaErrorInvalidValue;
+  } else {
+    const bool prep = c.prepare;
+    // shapes whose two CTAs fit an SM: E4 32 x 8 (depth 2 in FP32 only), wider
+    // stencils 32 x 4
+    if constexpr (ST == 4) {
+      if (c.bx == 32 && c.by == 8 && c.depth == 1) return launch_moment_elem<P, 4, 32, 8, 1>(d, c.zchunk, prep, s);
+      if constexpr (P == kF32)
+        if (c.bx == 32 && c.by == 8 && c.depth == 2) return launch_moment_elem<P, 4, 32, 8, 2>(d, c.zchunk, prep, s);
+    } else {
+      if (c.bx == 32 && c.by == 4 && c.depth == 1) return launch_moment_elem<P, ST, 32, 4, 1>(d, c.zchunk, prep, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+}
+
 template <int P, int ST>
 static cudaError_t dispatch_async(const LatticeDesc& d, TileCfg c, cudaStream_t s) {
   if constexpr (P == kF16) {
@@ -264,14 +318,24 @@ static cudaError_t launch_batch_variant(const BatchEntry* table, const BatchHead
   return cudaGetLastError();
 }
 
-template <int P, int ST, int BX, int BY, int D>
+template <int P, int ST, int BX, int BY, int D, bool ELEM = false>
 static cudaError_t launch_moment_batch_variant(const BatchEntry* table, const BatchHeader* hdr, int step,
                                                bool prepare, int* grid, cudaStream_t s) {
-  using Sh = MomentShape<P, ST, BX, BY, D>;
-  auto kern = lattice_moment_batch_kernel<P, ST, BX, BY, D>;
+  using Sh = MomentShape<P, ST, BX, BY, D, ELEM>;
+  auto kern = lattice_moment_batch_kernel<P, ST, BX, BY, D, ELEM>;
   static int resident = 0;
   if (prepare || resident == 0) {
     cudaError_t e = prepare_persistent(kern, Sh::NT, Sh::smem_bytes, &resident);
+    if constexpr (ELEM) {   // two CTAs per SM, the rest of the SM's memory left to L1
+      static_assert(2 * (Sh::smem_bytes + 1024) <= 228 * 1024, "two CTAs of kind 6 must fit an SM");
+      const int pct = (int)((2 * (Sh::smem_bytes + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+      int per_sm = 0, dev = 0, sms = 0;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Sh::NT, Sh::smem_bytes);
+      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) resident = (per_sm < 2 ? (per_sm > 0 ? per_sm : 1) : 2) * sms;
+    }
     if (e != cudaSuccess) return e;
   }
   if (grid) *grid = resident;
@@ -289,9 +353,17 @@ static cudaError_t dispatch_batch(int mode, const BatchEntry* table, const Batch
     return cudaErrorInvalidValue;
   } else if constexpr (P == kF32 && ST == 4) {
     if (mode == kBatchMoment) return launch_moment_batch_variant<P, ST, 32, 8, 1>(table, hdr, step, prepare, grid, s);
+    if (mode == kBatchMomentElem)
+      return launch_moment_batch_variant<P, ST, 32, 8, 1, true>(table, hdr, step, prepare, grid, s);
     if (mode == kBatchUnitTau) return launch_batch_variant<P, ST, 32, 8, 1, false>(table, hdr, step, prepare, grid, s);
     return launch_batch_variant<P, ST, 32, 8, 1, true>(table, hdr, step, prepare, grid, s);
   } else {
+    if (mode == kBatchMomentElem) {
+      if constexpr (ST == 4)   // FP64 E4: 32 x 8 tiles (the kind-6 shape)
+        return launch_moment_batch_variant<P, ST, 32, 8, 1, true>(table, hdr, step, prepare, grid, s);
+      else
+        return launch_moment_batch_variant<P, ST, 32, 4, 1, true>(table, hdr, step, prepare, grid, s);
+    }
     if (mode == kBatchMoment) return launch_moment_batch_variant<P, ST, 32, 4, 1>(table, hdr, step, prepare, grid, s);
     if (mode == kBatchUnitTau) return launch_batch_variant<P, ST, 32, 4, 1, false>(table, hdr, step, prepare, grid, s);
     return launch_batch_variant<P, ST, 32, 4, 1, true>(table, hdr, step, prepare, grid, s);
@@ -344,6 +416,12 @@ static cudaError_t dispatch_lattice(int stencil, int mode, const LatticeDesc& d,
     if (stencil == 4) return dispatch_bulk<P, 4>(d, c, s);
     if (stencil == 6) return dispatch_bulk<P, 6>(d, c, s);
     if (stencil == 8) return dispatch_bulk<P, 8>(d, c, s);
+    return cudaErrorInvalidValue;
+  }
+  if (mode == kModeStep && c.kind == 6) {
+    if (stencil == 4) return dispatch_moment_elem<P, 4>(d, c, s);
+    if (stencil == 6) return dispatch_moment_elem<P, 6>(d, c, s);
+    if (stencil == 8) return dispatch_moment_elem<P, 8>(d, c, s);
     return cudaErrorInvalidValue;
   }
   if (mode == kModeStep && c.kind == 5) {

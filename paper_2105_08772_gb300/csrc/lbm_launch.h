@@ -102,6 +102,17 @@ constexpr int kMomentE4[kNumMomentE4][3] = {{32, 8, 1}, {32, 8, 2}, {32, 4, 1}, 
 constexpr int kNumMomentWide = 1;
 constexpr int kMomentWide[kNumMomentWide][3] = {{32, 4, 1}};
 
+// the moment kernel with element copies (kind 6): 1 + depth stages of 19 padded
+// planes of the stored type, psi ring of 2R + 2 padded planes
+constexpr size_t moment_elem_smem_bytes(size_t stored, size_t arith, int R, int bx, int by, int depth) {
+  return ((size_t)(1 + depth) * Q * stored + (size_t)(2 * R + 2) * arith) * (bx + 2 * R) * (by + 2 * R);
+}
+
+// kind 6 runs 2 CTAs per SM (228 KB of shared memory, 1 KB reserved per CTA)
+constexpr bool moment_elem_two_per_sm(size_t elem, int R, int bx, int by, int depth) {
+  return 2 * (moment_elem_smem_bytes(elem, elem, R, bx, by, depth) + 1024) <= 228 * 1024;
+}
+
 constexpr size_t kMaxSmemPerCta = 227 * 1024;   // opt-in limit of one CTA on sm_103
 
 // number of CTAs (= FieldPartial records) a kind-0 lattice launch uses
@@ -117,10 +128,12 @@ struct BatchHeader;
 // prepare readies the kernel outside capture and reports the grid it uses
 // batch kernel modes: lattices with mixed tau, all tau = 1, or all tau = 1 with
 // boxes the moment kernel takes (nx % 4 == 0, nx >= tile width + 8)
-enum BatchMode : int { kBatchMixedTau = 0, kBatchUnitTau = 1, kBatchMoment = 2 };
+// (kBatchMomentElem: all tau = 1, some box not split into 16-byte row chunks: the
+// moment kernel with element copies)
+enum BatchMode : int { kBatchMixedTau = 0, kBatchUnitTau = 1, kBatchMoment = 2, kBatchMomentElem = 3 };
 inline TileCfg batch_tile(int prec, int stencil, int mode) {
-  TileCfg t{32, (prec == kF32 && stencil == 4) ? 8 : 4, 0};
-  t.kind = mode == kBatchMoment ? 5 : 1;
+  TileCfg t{32, (stencil == 4 && (prec == kF32 || mode == kBatchMomentElem)) ? 8 : 4, 0};
+  t.kind = mode == kBatchMoment ? 5 : (mode == kBatchMomentElem ? 6 : 1);
   return t;
 }
 cudaError_t launch_batch_f64(int stencil, int mode, const BatchEntry* table, const BatchHeader* hdr,

@@ -415,3 +415,39 @@ def test_f16_moment_kernel_parity(droplet_state_48):
     ab = np.max(np.abs(ra - rb) / rho_ref)
     print(f"f16 moment kernel: max relative density error {rel:.3e}; vs register-load kernel {ab:.3e}")
     assert np.isfinite(rel) and rel < 1e-2 and ab < 1e-2
+
+
+@pytest.mark.parametrize("prec,code,tau,shape", [(p, c, 1.0, sh) for p in ("f64", "f32")
+                                                 for c in (632080001, 632080002)
+                                                 for sh in ((13, 22, 72), (11, 21, 37))
+                                                 if not (p == "f64" and c == 632080002)]
+                         + [("f32", 632080001, 0.8, (11, 21, 37))])
+def test_moment_elem_kernel_matches_pipelined_kernel_and_oracle(prec, code, tau, shape):
+    """Kind 6: the moment kernel with element copies (any nx, here also odd, as the
+    paper's boxes are).  Bitwise equal to the pipelined kernel, and to the oracle;
+    tau != 1 runs the pipelined kernel under the same code.  (FP64 with prefetch
+    depth 2 does not fit two CTAs per SM and is not offered.)"""
+    f0 = inputs.random_populations(shape, seed=29)
+    a = lattice(shape, prec=prec, tau=tau)
+    a.set_populations(f0)
+    a.set_tile(code)
+    a.step(130)
+    b = lattice(shape, prec=prec, tau=tau)
+    b.set_populations(f0)
+    b.set_tile(132080001)
+    b.step(130)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    if prec == "f64":
+        ref = lbm3d.run(f0, oracle_model(tau=tau), 130)
+        assert np.max(np.abs(a.get_populations() - ref)) < 1e-12
+
+
+def test_moment_elem_kernel_wide_stencil():
+    shape = (9, 10, 37)
+    f0 = inputs.random_populations(shape, seed=30)
+    a = lattice(shape, stencil="E6")
+    a.set_populations(f0)
+    a.set_tile(632040001)
+    a.step(40)
+    ref = lbm3d.run(f0, oracle_model(stencil="E6"), 40)
+    assert np.max(np.abs(a.get_populations() - ref)) < 1e-12
