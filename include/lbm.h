@@ -221,14 +221,20 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int reps, long long* choice);
  * kind * 10^8 + bx * 10^6 + by * 10^4 + (kind ? z chunk * 10 + prefetch depth : z chunk),
  * kind 0 the register-load kernel, 1 the cp.async-pipelined kernel, 2 the row-bulk
  * pipelined kernel, 4 the pipelined kernel with 16-byte row chunks, 5 the unit-tau
- * moment kernel (for tau != 1 the same code runs kind 4).  Kinds 1-4: F32/F64
- * storage only, z chunk 0 = chosen by the launcher; 2, 4 and 5 need nx % 4 == 0
- * and nx >= bx + 8.  Kind 5 also takes F16 storage (E4, 32 x 8 tiles, tau = 1,
+ * moment kernel (for tau != 1 the same code runs kind 4), 6 the unit-tau moment
+ * kernel fed by element copies (any nx; two CTAs per SM; for tau != 1 the same
+ * code runs kind 1).  Kinds 1-4 and 6: F32/F64 storage only, z chunk 0 = chosen
+ * by the launcher; 2, 4 and 5 need nx % 4 == 0 and nx >= bx + 8; 6 is compiled
+ * for 32 x 8 tiles with E4 (depth 1, and depth 2 in F32) and 32 x 4 with E6/E8
+ * (depth 1).  Kind 5 also takes F16 storage (E4, 32 x 8 tiles, tau = 1,
  * nx % 8 == 0, nx >= 48).  The default (lbm_create) is kind 5 where it applies,
- * else kind 1 (kind 0 for F16).  A code that is not compiled for this context's
- * precision, stencil and box gives LBM_EINVAL.  lbm_get_tile returns the current
- * code.  Results do not depend on the choice: all kinds do the same arithmetic
- * per node and give bitwise-equal fields. */
+ * else kind 6, else kind 1 (kind 5 or 0 for F16).  A code that is not compiled
+ * for this context's precision, stencil and box gives LBM_EINVAL.  lbm_get_tile
+ * returns the current code.  In F32/F64 storage results do not depend on the
+ * choice: all kinds do the same arithmetic per node and give bitwise-equal
+ * fields.  In F16 storage kinds 5 and 0 sum in different orders, which FP16
+ * rounding of the stored populations makes visible (same bound to the FP64
+ * result). */
 lbm_status lbm_set_tile(lbm_ctx* ctx, long long code);
 lbm_status lbm_get_tile(const lbm_ctx* ctx, long long* code);
 
