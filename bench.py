@@ -232,9 +232,11 @@ def main():
     ap.add_argument("--no-sweep-leg", action="store_true")
     ap.add_argument("--no-large-leg", action="store_true")
     ap.add_argument("--kernel-only", action="store_true",
-                    help="build the 128^3 droplet lattice, run two single steps and exit "
+                    help="build one droplet lattice (128^3 unless --box), run two single steps and exit "
                          "(a small, fixed launch sequence for ncu captures)")
     ap.add_argument("--tile", type=int, default=0, help="tile code for --kernel-only (0: default)")
+    ap.add_argument("--box", type=int, default=SIZE,
+                    help="cubic box side for --kernel-only (odd sides take the element-copy kernel)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -252,14 +254,15 @@ def main():
     import paper_2105_08772_gb300 as P
 
     if args.kernel_only:
-        lat = P.Lattice(SIZE, SIZE, SIZE, tau=TAU, G=G, psi="one_minus_exp", stencil="E4", prec=args.prec)
-        lat.init_drop((SIZE // 2,) * 3, RADIUS, RHO_L, RHO_G)
+        L = args.box
+        lat = P.Lattice(L, L, L, tau=TAU, G=G, psi="one_minus_exp", stencil="E4", prec=args.prec)
+        lat.init_drop((L // 2,) * 3, RADIUS * L / SIZE, RHO_L, RHO_G)
         if args.tile:
             lat.set_tile(args.tile)
         lat.step(1)
         lat.step(1)
         torch.cuda.synchronize()
-        print(json.dumps({"kernel_only": True, "tile": lat.get_tile(), "prec": args.prec}))
+        print(json.dumps({"kernel_only": True, "box": L, "tile": lat.get_tile(), "prec": args.prec}))
         return
 
     dev = torch.cuda.current_device()
