@@ -137,8 +137,13 @@ __device__ __forceinline__ void load_plane(const LatticeDesc& d, int x0, int y0,
 // not with the psi values.  (Summing the 18 terms one by one in raster order
 // lets FP32 rounding build a spurious force that grows the density error of a
 // 1000-step droplet run tenfold.)
-template <typename T, int ST, int PX>
-__device__ __forceinline__ void sc_force_pairs(const T* const* planes, T G, T& Fx, T& Fy, T& Fz) {
+// OWN: own[dz + R] holds psi of the node's own column at offset dz (the caller
+// formed those values and kept them in registers); the centre and the pairs
+// along z take them from there instead of from shared memory.  Same values,
+// same order of operations.
+template <typename T, int ST, int PX, bool OWN = false>
+__device__ __forceinline__ void sc_force_pairs(const T* const* planes, T G, T& Fx, T& Fy, T& Fz,
+                                               const T* own = nullptr) {
   constexpr int R = stencil_radius<ST>();
   T sx = 0, sy = 0, sz = 0;
 #pragma unroll
@@ -151,7 +156,9 @@ __device__ __forceinline__ void sc_force_pairs(const T* const* planes, T G, T& F
         const bool upper = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
         const double Wd = shell_weight<ST>(dx * dx + dy * dy + dz * dz);
         if (upper && Wd != 0.0) {
-          const T d = planes[R + dz][dy * PX + dx] - planes[R - dz][-dy * PX - dx];
+          const T d = (OWN && dx == 0 && dy == 0)
+                          ? own[R + dz] - own[R - dz]
+                          : planes[R + dz][dy * PX + dx] - planes[R - dz][-dy * PX - dx];
           const T Wdiff = (T)Wd * d;
           if (dx != 0) sx += (T)dx * Wdiff;
           if (dy != 0) sy += (T)dy * Wdiff;
@@ -160,7 +167,7 @@ __device__ __forceinline__ void sc_force_pairs(const T* const* planes, T G, T& F
       }
     }
   }
-  const T k = -G * (T)(1.0 / 3.0) * planes[R][0];
+  const T k = -G * (T)(1.0 / 3.0) * (OWN ? own[R] : planes[R][0]);
   Fx = k * sx;
   Fy = k * sy;
   Fz = k * sz;

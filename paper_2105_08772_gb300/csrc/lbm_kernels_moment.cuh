@@ -215,6 +215,12 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
   T mdn[R + 1], mjx[R + 1], mjy[R + 1], mjz[R + 1];
 #pragma unroll
   for (int r = 0; r <= R; ++r) mdn[r] = mjx[r] = mjy[r] = mjz[r] = (T)0;
+  // psi of the own interior node for the last 2R + 1 planes: pz[2R] newest; at
+  // the collision of plane qc, pz[dz + R] is plane qc + dz (the force's own
+  // column and centre, kept in registers)
+  T pz[2 * R + 1];
+#pragma unroll
+  for (int r = 0; r <= 2 * R; ++r) pz[r] = (T)0;
 
   __syncthreads();   // the previous item's readers are done with every stage and psi plane
 #pragma unroll 1
@@ -240,7 +246,7 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
 #pragma unroll
       for (int dz = -R; dz <= R; ++dz) planes[dz + R] = ring + ((qc + dz) % NR) * NPAD + j0;
       T Fx, Fy, Fz;
-      sc_force_pairs<T, ST, PX>(planes, G, Fx, Fy, Fz);
+      sc_force_pairs<T, ST, PX, true>(planes, G, Fx, Fy, Fz, pz);
       const T dn = mdn[R];       // plane qc = qd - 1 - R: R planes before the newest
       const T n = n0 + dn;
       const T inv_n = (T)1 / n;
@@ -260,6 +266,8 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
       mjy[r] = mjy[r - 1];
       mjz[r] = mjz[r - 1];
     }
+#pragma unroll
+    for (int r = 0; r < 2 * R; ++r) pz[r] = pz[r + 1];
     if (qd < nplanes) {  // densities, psi and own moments of plane qd
       const S* st = stages + (qd % NS) * Sh::stage_elems;
       T* rs = ring + (qd % NR) * NPAD;
@@ -275,7 +283,9 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
         }
         T dn, jx, jy, jz;
         moments(v, dn, jx, jy, jz);
-        rs[j0] = psi_of<T>(n0 + dn, d.eos);
+        const T p = psi_of<T>(n0 + dn, d.eos);
+        rs[j0] = p;
+        pz[2 * R] = p;
         mdn[0] = dn;
         mjx[0] = jx;
         mjy[0] = jy;
