@@ -26,6 +26,7 @@ Everything is numpy float64, written to be read against the paper:
                      R_s, sigma_s and the Tolman fit (Eqs. (2), (12)).
 
 Parity status of each function is stated in its module docstring; the
-3-D transient itself is "parity unpinned" beyond the invariants the paper
-fixes (the paper prints no field values).
+3-D transient is pinned by invariants and by the closed forms of linear
+acoustics (sound speed from Eq. (10), damping from the lattice viscosity); the
+paper prints no field values.
 """
