@@ -238,6 +238,13 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int reps, long long* choice);
 lbm_status lbm_set_tile(lbm_ctx* ctx, long long code);
 lbm_status lbm_get_tile(const lbm_ctx* ctx, long long* code);
 
+/* The code (as for lbm_set_tile) of the step kernel configuration that
+ * lbm_create starts from for these arguments, without a context or a device:
+ * host only, so it also answers on machines without a GPU.  LBM_EINVAL for a
+ * null code, an invalid stencil or precision, a box that lbm_create rejects, or
+ * tau <= 1/2. */
+lbm_status lbm_default_tile(lbm_box box, int stencil, int prec, double tau, long long* code);
+
 /* Shift n0 and storage scale of the populations (F32/F16 modes; 0 and 1 for F64). */
 lbm_status lbm_storage_params(const lbm_ctx* ctx, double* n0, double* scale);
 

@@ -28,6 +28,7 @@ EXPORTS = (
     "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_run_to_convergence",
     "lbm_observables", "lbm_rho_profile", "lbm_pt_profile", "lbm_sigma_of_R", "lbm_copy_rho",
     "lbm_copy_velocity", "lbm_save", "lbm_load", "lbm_autotune", "lbm_set_tile", "lbm_get_tile",
+    "lbm_default_tile",
     "lbm_storage_params", "lbm_density_moments_noalloc", "lbm_batch_workspace_bytes",
     "lbm_batch_create", "lbm_batch_enqueue", "lbm_batch_run", "lbm_batch_result",
     "lbm_batch_last_error", "lbm_batch_destroy", "lbm_pn_profile", "lbm_flat_workspace_bytes",
@@ -94,6 +95,7 @@ def _load():
         "lbm_autotune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong)]),
         "lbm_set_tile": (C.c_int, [_P, C.c_longlong]),
         "lbm_get_tile": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
+        "lbm_default_tile": (C.c_int, [lbm_box, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_longlong)]),
         "lbm_storage_params": (C.c_int, [_P, _D, _D]),
         "lbm_strerror": (C.c_char_p, [C.c_int]),
         "lbm_last_error": (C.c_char_p, [_P]),

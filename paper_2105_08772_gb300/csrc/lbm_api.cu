@@ -978,6 +978,18 @@ lbm_status lbm_get_tile(const lbm_ctx* c, long long* code) {
   return LBM_OK;
 }
 
+lbm_status lbm_default_tile(lbm_box box, int stencil, int prec, double tau, long long* code) {
+  if (!code) return fail(nullptr, LBM_EINVAL, "code is null");
+  if (!valid_stencil(stencil)) return fail(nullptr, LBM_EINVAL, "stencil must be 4, 6 or 8");
+  if (!valid_prec(prec)) return fail(nullptr, LBM_EINVAL, "prec must be 0, 1 or 2");
+  if (!box_ok(box, stencil))
+    return fail(nullptr, LBM_EINVAL, "box %dx%dx%d too small (sides >= %d)", box.nx, box.ny, box.nz,
+                2 * radius_of(stencil) + 1);
+  if (!(tau > 0.5) || !isfinite(tau)) return fail(nullptr, LBM_EINVAL, "tau must be > 1/2");
+  *code = tile_code(default_tile(box, prec, stencil, tau));
+  return LBM_OK;
+}
+
 lbm_status lbm_storage_params(const lbm_ctx* c, double* n0, double* scale) {
   if (!c) return fail(nullptr, LBM_EINVAL, "null context");
   if (n0) *n0 = c->n0;

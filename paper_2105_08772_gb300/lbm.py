@@ -148,6 +148,17 @@ def lbm_get_tile(ctx) -> int:
     return code.value
 
 
+def lbm_default_tile(box: lbm_box, stencil: int, prec: int, tau: float = 1.0) -> int:
+    """Tile code lbm_create starts from for these arguments (host only, no device)."""
+    code = C.c_longlong(0)
+    check(_lib_.lbm_default_tile(box, int(stencil), int(prec), float(tau), C.byref(code)), None)
+    return code.value
+
+
+def default_tile(nx: int, ny: int, nz: int, stencil="E4", prec="f32", tau=1.0) -> int:
+    return lbm_default_tile(make_box(nx, ny, nz), STENCILS[stencil], PRECS[prec], tau)
+
+
 def lbm_storage_params(ctx) -> tuple[float, float]:
     n0 = C.c_double()
     sc = C.c_double()

@@ -144,3 +144,42 @@ def test_coexistence_estimate_rejects_no_loop():
         P.coexistence_estimate(-3.9)             # above G_c = -4: no van der Waals loop
     with pytest.raises(P.LBMError):
         P.coexistence_estimate(-7.0)             # the construction's gas density has reached 0
+
+
+@pytest.mark.parametrize("box,stencil,prec,tau,code", [
+    # row chunks (nx % 4 == 0, nx >= 40): the moment kernel, 32 x 8 for E4 ...
+    ((128, 128, 128), "E4", "f32", 1.0, 532080001),
+    ((156, 156, 156), "E4", "f32", 1.0, 532080001),    # 3.8M nodes: prefetch depth 1
+    ((160, 160, 160), "E4", "f32", 1.0, 532080002),    # 4.1M nodes: depth 2 in FP32
+    ((160, 160, 160), "E4", "f64", 1.0, 532080001),
+    ((128, 128, 128), "E4", "f32", 0.8, 532080001),    # same code; tau != 1 runs the chunked kernel
+    ((256, 256, 256), "E6", "f32", 1.0, 532040001),    # ... 32 x 4 for the wider stencils
+    # odd or narrow rows: the moment kernel with element copies
+    ((127, 127, 127), "E4", "f32", 1.0, 632080001),
+    ((158, 158, 158), "E4", "f32", 1.0, 632080001),
+    ((36, 36, 36), "E4", "f32", 1.0, 632080001),
+    ((16, 16, 16), "E4", "f64", 1.0, 632080001),
+    ((255, 255, 255), "E8", "f64", 1.0, 632040001),
+    # FP16: the moment kernel with an FP16 stage (E4, tau = 1, nx % 8 == 0, nx >= 48),
+    # else the register-load kernel (kind 0, z chunk 16)
+    ((128, 128, 128), "E4", "f16", 1.0, 532080002),
+    ((128, 128, 128), "E4", "f16", 0.8, 32080016),
+    ((40, 40, 40), "E4", "f16", 1.0, 32080016),
+])
+def test_default_tile_policy(box, stencil, prec, tau, code):
+    """The kernel choice lbm_create starts from, queried on the host."""
+    assert P.default_tile(*box, stencil=stencil, prec=prec, tau=tau) == code
+
+
+@pytest.mark.parametrize("args", [
+    ((64, 64, 64), 5, _lib.LBM_F32_SHIFTED, 1.0),
+    ((64, 64, 64), _lib.LBM_E4, 3, 1.0),
+    ((64, 64, 64), _lib.LBM_E4, _lib.LBM_F32_SHIFTED, 0.5),
+    ((2, 64, 64), _lib.LBM_E4, _lib.LBM_F32_SHIFTED, 1.0),
+    ((64, 64, 4), _lib.LBM_E6, _lib.LBM_F32_SHIFTED, 1.0),
+])
+def test_default_tile_rejects_what_create_rejects(args):
+    box, stencil, prec, tau = args
+    with pytest.raises(_lib.LBMError) as e:
+        P.lbm_default_tile(P.make_box(*box), stencil, prec, tau)
+    assert e.value.status == _lib.LBM_EINVAL
