@@ -14,7 +14,10 @@
 //
 // Copies: the 16-byte row chunks of the chunked kernel (lbm_kernels_chunk.cuh),
 // staged in the storage type (FP16 storage: half the shared memory, a 16-byte
-// chunk is 8 values, so the apron is 8 and nx % 8 == 0 is needed).
+// chunk is 8 values, so the apron is 8 and nx % 8 == 0 is needed); or, for
+// rows that do not split into chunks (odd or narrow nx; ELEM), the pipelined
+// kernel's 4/8-byte element copies of each pulled population straight to its
+// padded node, two CTAs per SM so that L1 keeps room for them.
 // Thread roles in the density pass: each thread forms its own column's padded
 // node (ty + R, tx + R) -- its interior node, whose moments it keeps -- and
 // the NPAD - NT nodes of the halo ring are dealt out to the threads (to warps
