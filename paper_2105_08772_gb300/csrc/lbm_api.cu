@@ -13,6 +13,8 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbm.h"
 #include "lbm_launch.h"
 
@@ -52,6 +54,15 @@ struct lbm_ctx {
   lbm_obs last;
   int have_last;
   char err[512];
+};
+
+// Named ranges on a profiler's timeline around the calls that drive the device
+// (NVTX; without a tool attached each is a null check).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 namespace {
@@ -653,6 +664,7 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* host_f) {
 }
 
 lbm_status lbm_step(lbm_ctx* c, long long n) {
+  NvtxRange nvtx("lbm_step");
   LBM_CHECK_CTX(c);
   LBM_CHECK_INIT(c);
   if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
@@ -670,6 +682,7 @@ lbm_status lbm_step(lbm_ctx* c, long long n) {
 }
 
 lbm_status lbm_observables(lbm_ctx* c, lbm_obs* out) {
+  NvtxRange nvtx("lbm_observables");
   LBM_CHECK_CTX(c);
   LBM_CHECK_INIT(c);
   lbm_status st = observe(c, nullptr, nullptr, 1, true);
@@ -685,6 +698,7 @@ lbm_status lbm_observables(lbm_ctx* c, lbm_obs* out) {
 lbm_status lbm_run_to_convergence(lbm_ctx* c, long long max_steps, long long check_every,
                                   double tol_dP_rel, double tol_du, long long* steps_done,
                                   int* criterion) {
+  NvtxRange nvtx("lbm_run_to_convergence");
   LBM_CHECK_CTX(c);
   LBM_CHECK_INIT(c);
   if (max_steps < 0 || check_every < 1) return fail(c, LBM_EINVAL, "max_steps >= 0, check_every >= 1");
@@ -1466,6 +1480,7 @@ lbm_status lbm_batch_enqueue(lbm_batch* b, lbm_box box, double tau, double G, lb
 
 lbm_status lbm_batch_run(lbm_batch* b, long long max_steps, long long check_every, double tol_dP_rel,
                          double tol_du, long long* lattice_updates) {
+  NvtxRange nvtx("lbm_batch_run");
   if (!b) return bfail(nullptr, LBM_EINVAL, "null batch");
   if (max_steps < 0 || check_every < 2) return bfail(b, LBM_EINVAL, "max_steps >= 0, check_every >= 2");
   const int K = (int)(check_every + (check_every & 1));   // even: a graph keeps every parity
@@ -1667,6 +1682,7 @@ void lbm_group_destroy(lbm_group* g) {
 }
 
 lbm_status lbm_group_step(lbm_group* g, long long n) {
+  NvtxRange nvtx("lbm_group_step");
   if (!g) return gfail(nullptr, LBM_EINVAL, "null group");
   if (n < 0) return gfail(g, LBM_EINVAL, "n must be >= 0");
   for (lbm_ctx* c : g->ctx)
