@@ -146,12 +146,17 @@ lbm_status lbm_init_drop(lbm_ctx* ctx, const double center[3], double R,
 
 /* Initialise from a host density field (nx*ny*nz doubles, layout above), fluid at
  * rest.  The field is copied to the device inside the call (the host buffer may be
- * reused on return).  For shifted storage the shift n0 is the field's mean. */
+ * reused on return).  For shifted storage the shift n0 is the field's mean.
+ * LBM_EINVAL (nothing enqueued) for a null buffer or a density that is not
+ * positive and finite. */
 lbm_status lbm_init_rho(lbm_ctx* ctx, const double* host_rho);
 
 /* Set / get the pre-collision populations f_i(x, t) of Eq. (3) from / to a host
  * buffer of 19*nx*ny*nz doubles (layout above).  set resets the step counter; for
- * shifted storage the shift n0 is the field's mean density.  get synchronises. */
+ * shifted storage the shift n0 is the field's mean density; it takes any finite
+ * values (LBM_EINVAL for a null buffer or a non-finite value), and a field the
+ * step cannot carry (a non-positive or overflowing density) is reported as
+ * LBM_ENUMERIC by the next convergence check.  get synchronises. */
 lbm_status lbm_set_populations(lbm_ctx* ctx, const double* host_f);
 lbm_status lbm_get_populations(lbm_ctx* ctx, double* host_f);
 
