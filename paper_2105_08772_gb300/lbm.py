@@ -283,7 +283,9 @@ def lbm_batch_destroy(b) -> None:
 
 
 class Batch:
-    """A batch of lattices on a torch-owned workspace (see lbm_batch_* in include/lbm.h)."""
+    """A batch of lattices on a torch-owned workspace (see lbm_batch_* in include/lbm.h).
+    Stream rule as for Lattice: allocate under the stream the batch runs on, or
+    synchronise that stream before the batch is closed."""
 
     def __init__(self, slots: int, max_box, stencil="E4", prec="f32", stream=None):
         import torch
@@ -381,7 +383,13 @@ class Group:
 
 @dataclass
 class Lattice:
-    """One lattice: a torch-owned device workspace plus an lbm_ctx on a stream."""
+    """One lattice: a torch-owned device workspace plus an lbm_ctx on a stream.
+
+    The workspace is allocated on torch's current stream.  When `stream` is a
+    different stream, create the lattice inside `with torch.cuda.stream(stream):`
+    (as bench.py does), or synchronise `stream` before the lattice is closed or
+    dropped: otherwise torch's caching allocator may hand the memory to other
+    work while kernels queued on `stream` still use it."""
     nx: int
     ny: int
     nz: int
