@@ -94,3 +94,13 @@ def test_power_law_recovers_exponent():
     assert A == pytest.approx(0.3, rel=1e-12) and lam == pytest.approx(-1.0, abs=1e-12)
     A, lam = S.power_law([0.1, 0.2, 0.3], [-1.0, 2.0, 1.0])   # non-positive delta left out
     assert lam == pytest.approx(np.log(0.5) / np.log(1.5))
+
+
+def test_paper_lists_match_the_printed_values():
+    """The sweep's reduced couplings and box sides are the ones Sec. IV prints
+    (tests/golden/paper_constants.json, with its citations)."""
+    import json
+    from pathlib import Path
+    g = json.loads((Path(__file__).parent / "golden" / "paper_constants.json").read_text())
+    assert list(S.PAPER_EPS) == g["reduced_couplings"]["values"]
+    assert list(S.PAPER_L) == g["box_sizes"]["values"]
