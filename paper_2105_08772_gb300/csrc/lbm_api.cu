@@ -483,7 +483,7 @@ lbm_status lbm_create(lbm_box box, double tau, double G, lbm_eos eos, int stenci
   if (!valid_stencil(stencil)) return fail(nullptr, LBM_EINVAL, "stencil must be 4, 6 or 8");
   if (!valid_prec(prec)) return fail(nullptr, LBM_EINVAL, "prec must be 0, 1 or 2");
   if (!box_ok(box, stencil))
-    return fail(nullptr, LBM_EINVAL, "box %dx%dx%d too small (sides >= %d)", box.nx, box.ny, box.nz,
+    return fail(nullptr, LBM_EINVAL, "box %dx%dx%d not allowed (sides >= %d, below 2^31 nodes)", box.nx, box.ny, box.nz,
                 2 * radius_of(stencil) + 1);
   if (!(tau > 0.5) || !isfinite(tau)) return fail(nullptr, LBM_EINVAL, "tau must be > 1/2");
   if (!isfinite(G)) return fail(nullptr, LBM_EINVAL, "G must be finite");
@@ -997,7 +997,7 @@ lbm_status lbm_default_tile(lbm_box box, int stencil, int prec, double tau, long
   if (!valid_stencil(stencil)) return fail(nullptr, LBM_EINVAL, "stencil must be 4, 6 or 8");
   if (!valid_prec(prec)) return fail(nullptr, LBM_EINVAL, "prec must be 0, 1 or 2");
   if (!box_ok(box, stencil))
-    return fail(nullptr, LBM_EINVAL, "box %dx%dx%d too small (sides >= %d)", box.nx, box.ny, box.nz,
+    return fail(nullptr, LBM_EINVAL, "box %dx%dx%d not allowed (sides >= %d, below 2^31 nodes)", box.nx, box.ny, box.nz,
                 2 * radius_of(stencil) + 1);
   if (!(tau > 0.5) || !isfinite(tau)) return fail(nullptr, LBM_EINVAL, "tau must be > 1/2");
   *code = tile_code(default_tile(box, prec, stencil, tau));
@@ -1420,7 +1420,7 @@ lbm_status lbm_batch_create(int slots, lbm_box max_box, int stencil, int prec, v
   if (slots < 1) return bfail(nullptr, LBM_EINVAL, "slots must be >= 1");
   if (!valid_stencil(stencil) || !valid_prec(prec) || prec == kF16)
     return bfail(nullptr, LBM_EINVAL, "batches need stencil 4/6/8 and F64 or F32 storage");
-  if (!box_ok(max_box, stencil)) return bfail(nullptr, LBM_EINVAL, "max_box too small");
+  if (!box_ok(max_box, stencil)) return bfail(nullptr, LBM_EINVAL, "max_box not allowed (sides >= 2R + 1, below 2^31 nodes)");
   const BatchLayout L = batch_layout(slots, max_box, stencil, prec);
   if (!dev_workspace) return bfail(nullptr, LBM_EINVAL, "workspace is null");
   if (((uintptr_t)dev_workspace & 255) != 0) return bfail(nullptr, LBM_EINVAL, "workspace not 256-byte aligned");

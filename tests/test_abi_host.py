@@ -62,6 +62,8 @@ def test_workspace_bytes():
     assert P.lbm_workspace_bytes(P.make_box(4, 8, 8), 6, 0) == 0     # too small for E6
     assert P.lbm_workspace_bytes(b, 5, 0) == 0                       # no such stencil
     assert P.lbm_workspace_bytes(b, 4, 7) == 0                       # no such precision
+    assert P.lbm_workspace_bytes(P.make_box(1300, 1300, 1300), 4, 1) == 0   # >= 2^31 nodes
+    assert P.lbm_workspace_bytes(P.make_box(1290, 1290, 1290), 4, 1) > 0
 
 
 def _create(**kw):
@@ -79,8 +81,10 @@ def _create(**kw):
     (dict(G=-3.9), _lib.LBM_EINVAL, "G_c = -4"),
     (dict(G=-7.0, eos=P.make_eos("exp_inv")), _lib.LBM_EINVAL, "exp(-1/n)"),
     (dict(tau=0.5), _lib.LBM_EINVAL, "tau"),
-    (dict(box=P.make_box(2, 16, 16)), _lib.LBM_EINVAL, "too small"),
-    (dict(box=P.make_box(4, 16, 16), stencil=8), _lib.LBM_EINVAL, "too small"),
+    (dict(box=P.make_box(2, 16, 16)), _lib.LBM_EINVAL, "sides >= 3"),
+    (dict(box=P.make_box(4, 16, 16), stencil=8), _lib.LBM_EINVAL, "sides >= 5"),
+    # node offsets inside a population plane are 32-bit in the kernels
+    (dict(box=P.make_box(1300, 1300, 1300)), _lib.LBM_EINVAL, "below 2^31 nodes"),
     (dict(stencil=5), _lib.LBM_EINVAL, "stencil"),
     (dict(prec=3), _lib.LBM_EINVAL, "prec"),
     (dict(ws=0), _lib.LBM_EINVAL, "null"),
