@@ -125,7 +125,8 @@ size_t lbm_workspace_bytes(lbm_box box, int stencil, int prec);
  * time of Eq. (4), > 1/2.  G: coupling of Eq. (8); for the two closed-form psi
  * kinds it must be below the critical coupling (-e^2 for exp(-1/n), -4 for
  * 1 - exp(-n); Sec. II below Eq. (10), Sec. IV), else LBM_EINVAL.  Box sides
- * must be >= 3 (E4) or >= 5 (E6/E8).  dev_workspace: caller-owned device
+ * must be >= 3 (E4) or >= 5 (E6/E8) and the box below 2^31 nodes (node offsets
+ * within a population plane are 32-bit).  dev_workspace: caller-owned device
  * memory of at least lbm_workspace_bytes bytes, else LBM_ENOMEM.
  * cuda_stream: cudaStream_t used for all work.  *out receives a host-side
  * context (free it with lbm_destroy).  The field is uninitialised until one of
