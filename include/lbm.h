@@ -365,15 +365,21 @@ void lbm_batch_destroy(lbm_batch* b);
  * n_ref: the outer density (e.g. lbm_obs.n_out); the centre of mass is that of
  * n - n_ref with minimum-image displacements about the centre node, as in
  * lbm_obs.com.  dev_out: device array of 4 doubles, written with
- * {sum_x n, com_x, com_y, com_z}.  Async on cuda_stream.
+ * {sum_x n, com_x, com_y, com_z}.  Async on cuda_stream.  When
+ * sum_x (n - n_ref) is exactly 0 (a field uniform at n_ref, say) there is no
+ * centre of mass and com_x, com_y, com_z are NaN; the mass is still written.
  *
  * No device memory is allocated: per-block partial sums go to a fixed scratch
  * array inside the library (160 KiB per device, held until the process exits).
  * Limit: nx*ny*nz <= 33554432 nodes (4096 partial sums of 8192 nodes); larger
- * fields, null pointers or sides < 1 return LBM_EINVAL with a message in
- * lbm_last_error(NULL).  The first call on a device looks up the scratch's
+ * fields, sides < 1 or null pointers (checked in that order) return LBM_EINVAL
+ * with a message in lbm_last_error(NULL).  The first call on a device looks up the scratch's
  * device address with that device current; make that first call before any
- * stream capture.  Every call shares the one scratch array, which keeps the
+ * stream capture.  The address is cached per device index for the life of the
+ * process: after a cudaDeviceReset (or anything else that destroys and
+ * re-creates the device's primary context) the cached address is stale, so do
+ * not call this entry point on a device that was reset after its first call.
+ * Every call shares the one scratch array, which keeps the
  * last call's partial sums (each call writes every record it reads, so nothing
  * needs clearing); calls that overlap on the GPU -- on two streams, say --
  * race on it and must be serialised by the caller. */

@@ -82,10 +82,13 @@ noalloc_finalize(const double* __restrict__ scratch, int nblocks, int nx, int ny
   double t[kNoallocRecord];
   for (int k = 0; k < kNoallocRecord; ++k) t[k] = block_sum(s[k], red);
   if (threadIdx.x == 0) {
+    // a field with no excess over n_ref (uniform at n_ref, or excess that
+    // cancels exactly) has no centre of mass: NaN, not a division by zero
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
     out[0] = t[0];
-    out[1] = (double)(nx / 2) + t[2] / t[1];
-    out[2] = (double)(ny / 2) + t[3] / t[1];
-    out[3] = (double)(nz / 2) + t[4] / t[1];
+    out[1] = t[1] != 0.0 ? (double)(nx / 2) + t[2] / t[1] : nan;
+    out[2] = t[1] != 0.0 ? (double)(ny / 2) + t[3] / t[1] : nan;
+    out[3] = t[1] != 0.0 ? (double)(nz / 2) + t[4] / t[1] : nan;
   }
 }
 
@@ -115,10 +118,8 @@ cudaError_t scratch_for_current_device(double** out) {
 
 extern "C" lbm_status lbm_density_moments_noalloc(const double* dev_rho, int nx, int ny, int nz,
                                                   double n_ref, double* dev_out, void* cuda_stream) {
-  if (!dev_rho || !dev_out) {
-    lbm::set_global_error("lbm_density_moments_noalloc: null device pointer");
-    return LBM_EINVAL;
-  }
+  // sizes first, then pointers: a null pointer at an accepted size reports the
+  // pointer, so the size limit can be checked without a device
   if (nx < 1 || ny < 1 || nz < 1) {
     lbm::set_global_error("lbm_density_moments_noalloc: box sides must be >= 1");
     return LBM_EINVAL;
@@ -128,6 +129,10 @@ extern "C" lbm_status lbm_density_moments_noalloc(const double* dev_rho, int nx,
     lbm::set_global_error(
         "lbm_density_moments_noalloc: field has more than 33554432 nodes (the fixed scratch "
         "holds 4096 partial sums of 8192 nodes each)");
+    return LBM_EINVAL;
+  }
+  if (!dev_rho || !dev_out) {
+    lbm::set_global_error("lbm_density_moments_noalloc: null device pointer");
     return LBM_EINVAL;
   }
   double* scratch = nullptr;
