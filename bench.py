@@ -137,59 +137,156 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def bench_reference(args):
-    """FP64 CPU oracle on the same workload: one LB step per lattice per bench step."""
-    import numpy as np  # noqa: F401
+def host_cpu():
+    """Core count and CPU model of this host (the oracle's timing runs on all of its cores)."""
+    import platform
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in Path("/proc/cpuinfo").read_text().splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"nproc": cores, "model": model or platform.machine()}
+
+
+def _mem_available_bytes():
+    try:
+        for line in Path("/proc/meminfo").read_text().splitlines():
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except Exception:
+        pass
+    return None
+
+
+ORACLE_BYTES_PER_LATTICE = 2.5e9     # peak resident set of one 128^3 oracle step (measured 1.5 GB)
+
+
+def _oracle_worker(conn, bubble):
+    """One process, one 128^3 oracle lattice (droplet or bubble); steps it on request."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import eos as E
     from oracle import lbm3d
+    m = lbm3d.Model(tau=TAU, G=G, eos=E.EOS("one_minus_exp"))
+    a, b = (RHO_G, RHO_L) if bubble else (RHO_L, RHO_G)
+    f = lbm3d.init_from_density(lbm3d.drop_density((SIZE,) * 3, (SIZE // 2,) * 3, RADIUS, a, b))
+    conn.send("ready")
+    while True:
+        k = conn.recv()
+        if k is None:
+            break
+        for _ in range(k):
+            f = lbm3d.step(f, m)
+        conn.send(k)
 
+
+class OraclePool:
+    """Independent 128^3 oracle lattices, one per host core (spawned processes, so the
+    pool is safe to start after CUDA is initialised); droplets and bubbles alternate."""
+
+    def __init__(self, workers=None):
+        import multiprocessing as mp
+        cpu = host_cpu()
+        n = workers or cpu["nproc"]
+        avail = _mem_available_bytes()
+        if avail:
+            n = max(1, min(n, int(0.8 * avail // ORACLE_BYTES_PER_LATTICE)))
+        self.cpu = cpu
+        self.workers = n
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for k in range(n):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, k % 2 == 1), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for c in self.conns:
+            assert c.recv() == "ready"
+
+    def step(self, k=1):
+        """k LB steps on every lattice; returns when all are done."""
+        for c in self.conns:
+            c.send(k)
+        for c in self.conns:
+            c.recv()
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(None)
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+            if p.is_alive():
+                p.kill()
+
+
+def bench_reference(args):
+    """FP64 CPU oracle on the same workload and metric, on every host core: one 128^3
+    lattice per core (droplets and bubbles alternating), one LB step of each per bench step."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    m = lbm3d.Model(tau=TAU, G=G, eos=E.EOS("one_minus_exp"))
-    c = (SIZE // 2,) * 3
-    lattices = [lbm3d.init_from_density(lbm3d.drop_density((SIZE,) * 3, c, RADIUS, a, b))
-                for a, b in ((RHO_L, RHO_G), (RHO_G, RHO_L))]
-
-    def one():
-        for k in range(len(lattices)):
-            lattices[k] = lbm3d.step(lattices[k], m)
-
-    for _ in range(args.warmup):
-        one()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        one()
-    dt = time.perf_counter() - t0
-    lu = len(lattices) * SIZE ** 3 * args.steps
+    pool = OraclePool()
+    try:
+        for _ in range(args.warmup):
+            pool.step(1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.step(1)
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+    lu = pool.workers * SIZE ** 3 * args.steps
     val = lu / dt / 1e6
     line = {
         "impl": "reference", "metric": "MLUPS", "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "reference_step": "1 LB step per lattice (bounded sample)"},
-        "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} x (1 LB step of each 128^3 lattice), numpy FP64"},
+        "config": {"workload": WORKLOAD,
+                   "reference_step": f"1 LB step of each of {pool.workers} 128^3 lattices (bounded sample)"},
+        "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": pool.workers, "kind": "oracle",
+                         "host": pool.cpu,
+                         "sample": f"{args.steps} x (1 LB step of each of {pool.workers} independent 128^3 "
+                                   f"lattices, one process per core), numpy FP64"},
         "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def cpu_baseline_sample(seconds_target=12.0):
-    """The oracle as it stands on this host: 128^3 lattice, whole LB steps until ~12 s."""
-    from oracle import eos as E
-    from oracle import lbm3d
-    m = lbm3d.Model(tau=TAU, G=G, eos=E.EOS("one_minus_exp"))
-    f = lbm3d.init_from_density(lbm3d.drop_density((SIZE,) * 3, (SIZE // 2,) * 3, RADIUS, RHO_L, RHO_G))
-    t0 = time.perf_counter()
-    n = 0
-    while time.perf_counter() - t0 < seconds_target or n == 0:
-        f = lbm3d.step(f, m)
-        n += 1
-    dt = time.perf_counter() - t0
-    return {"value": SIZE ** 3 * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{n} LB steps of the 128^3 droplet lattice, numpy FP64, single thread"}
+    """The oracle as it stands on every host core: one 128^3 lattice per core, whole LB
+    steps of all of them until about 12 s have passed."""
+    pool = OraclePool()
+    try:
+        pool.step(1)                      # first step outside the sample
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < seconds_target or n == 0:
+            pool.step(1)
+            n += 1
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+    return {"value": pool.workers * SIZE ** 3 * n / dt / 1e6, "unit": "MLUPS", "cores": pool.workers,
+            "kind": "oracle", "host": pool.cpu,
+            "sample": f"{n} LB steps of each of {pool.workers} independent 128^3 lattices "
+                      f"(one process per core), numpy FP64"}
 
 
 SWEEP_RADII = (18.0, 20.0, 22.0, 24.0)
