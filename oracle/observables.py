@@ -40,6 +40,11 @@ Readings (the paper is silent on them):
   closed form only by the quadrature of the P_T part (node trapezoid vs
   interpolated fine grid): below 1% for interfaces a few nodes wide.
 * Bubbles enter the Tolman fit with negative curvature (Sec. IV): R_s -> -R_s.
+* hat-delta (Sec. IV, last paragraph; Fig. 4): hat-delta_+- = +-(R_e - R_s), + for
+  droplets and - for bubbles.  Its flat limit is taken as the intercept of one
+  least-squares straight line in the signed curvature x = +-1/R_s through the
+  droplets and the bubbles together (the paper does not say how its flat-limit
+  points were obtained).
 * Collapse: |n_in - n_out| below 1e-2 of the initial contrast.
 
 Parity: Eq. (9) pinned by the uniform field (P = P(n) delta exactly) and the
@@ -251,6 +256,24 @@ def run_to_convergence(f, m: lbm3d.Model, max_steps=50_000, check_every=2048,
             break
         dP_prev, u_prev = obs.dP, u
     return RunResult(f, steps, crit, dP_hist, du_hist)
+
+
+def delta_hat(R_e, R_s, bubble):
+    """Sec. IV: hat-delta_+- = +-(R_e - R_s), + for droplets, - for bubbles."""
+    sign = np.where(np.asarray(bubble, dtype=bool), -1.0, 1.0)
+    return sign * (np.asarray(R_e, dtype=np.float64) - np.asarray(R_s, dtype=np.float64))
+
+
+def delta_hat_flat_limit(R_e, R_s, bubble):
+    """hat-delta at 1/R_s -> 0: intercept of the least-squares line of hat-delta_+-
+    against the signed curvature x = +-1/R_s (bubbles negative), droplets and
+    bubbles in one fit."""
+    R_s = np.asarray(R_s, dtype=np.float64)
+    b = np.asarray(bubble, dtype=bool)
+    x = np.where(b, -1.0, 1.0) / R_s
+    A = np.stack([np.ones_like(x), x], axis=1)
+    coef, *_ = np.linalg.lstsq(A, delta_hat(R_e, R_s, b), rcond=None)
+    return float(coef[0])
 
 
 def tolman_fit(R_s, sigma_s, bubble, quadratic=True):

@@ -146,3 +146,24 @@ def test_converged_droplet_satisfies_mechanical_equilibrium_moment(converged_sma
     r = np.arange(len(ob.PT_line))
     scale = np.trapezoid(2 * r * np.abs(ob.PT_line - ob.P_out), r)
     assert abs(2 * ob.D) < 0.05 * scale
+
+
+def test_delta_hat_signs_and_flat_limit():
+    """hat-delta_+- = +-(R_e - R_s) (Sec. IV).  With R_e - R_s = delta + k/R_s for droplets
+    and R_s - R_e = delta - k/R_s for bubbles -- one line delta + k x in the signed
+    curvature -- the flat limit is delta exactly; two runs fix it by hand."""
+    assert O.delta_hat(10.4, 10.0, False) == pytest.approx(0.4)
+    assert O.delta_hat(9.7, 10.0, True) == pytest.approx(0.3)
+    delta, k = 0.57, -1.9
+    Rs = np.array([8.0, 12.0, 17.0, 25.0, 9.0, 14.0, 21.0, 33.0])
+    bub = np.array([False] * 4 + [True] * 4)
+    x = np.where(bub, -1.0, 1.0) / Rs
+    Re = Rs + np.where(bub, -1.0, 1.0) * (delta + k * x)
+    assert O.delta_hat_flat_limit(Re, Rs, bub) == pytest.approx(delta, rel=1e-12)
+    # a droplet at R_s = 10 and a bubble at R_s = 20: the line through (0.1, h1) and
+    # (-0.05, h2) meets x = 0 at h2 + (h1 - h2) / 3
+    h1, h2 = 0.9, 0.6
+    got = O.delta_hat_flat_limit([10.0 + h1, 20.0 - h2], [10.0, 20.0], [False, True])
+    assert got == pytest.approx(h2 + (h1 - h2) / 3.0, rel=1e-12)
+    # the bubble sign matters: treating bubbles like droplets moves the limit
+    assert abs(O.delta_hat_flat_limit(Re, Rs, np.zeros(8, dtype=bool)) - delta) > 0.1

@@ -104,3 +104,20 @@ def test_paper_lists_match_the_printed_values():
     g = json.loads((Path(__file__).parent / "golden" / "paper_constants.json").read_text())
     assert list(S.PAPER_EPS) == g["reduced_couplings"]["values"]
     assert list(S.PAPER_L) == g["box_sizes"]["values"]
+
+
+def test_flat_limit_of_delta_hat_matches_the_oracle():
+    """sweep.tolman's hat-delta_0 against oracle.observables.delta_hat_flat_limit on the
+    same (noisy) outcomes."""
+    import numpy as np
+    from oracle import observables as O
+    rng = np.random.default_rng(3)
+    outs = []
+    for bubble in (False, True):
+        for Rs in (9.0, 12.5, 16.0, 21.0, 27.0, 35.0):
+            Re = Rs + (-1.0 if bubble else 1.0) * (0.8 + 0.1 * rng.standard_normal())
+            outs.append(_outcome(-5.0, bubble, Rs, 0.036 + 1e-3 * rng.standard_normal(), Re))
+    got = S.tolman(outs)[-5.0].delta_hat0
+    want = O.delta_hat_flat_limit([o.obs["R_e"] for o in outs], [o.obs["R_s"] for o in outs],
+                                  [o.run.bubble for o in outs])
+    assert got == pytest.approx(want, rel=1e-12)
