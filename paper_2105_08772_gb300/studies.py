@@ -1,4 +1,9 @@
-"""Two measurement studies on single lattices.
+"""Measurement studies on single lattices.
+
+configs: the plain-method workloads on one GPU -- a 32^3 FP64 droplet (R = 8,
+  2000 steps) and 128^3 droplets and bubbles (R = 32) in FP64 and shifted FP32 run
+  to the convergence tests of Sec. IV -- with R_e, Delta P, R_s, sigma_s, steps,
+  wall time and throughput per run.
 
 precision: one droplet per radius in an L^3 box (psi = 1 - exp(-n), E4), run to
   the convergence tests of Sec. IV with populations stored in FP64, shifted FP32
@@ -14,7 +19,8 @@ eos: the Carnahan-Starling-mapped pseudopotential (psi^2 = 2 (p_CS - n c_s^2) /
 Every run goes through liblbm.so on the GPU; this module only sequences the
 calls and compares the results.
 
-Command line:  python -m paper_2105_08772_gb300.studies precision --L 192
+Command line:  python -m paper_2105_08772_gb300.studies configs
+               python -m paper_2105_08772_gb300.studies precision --L 192
                python -m paper_2105_08772_gb300.studies eos --L 256 --R 48
 """
 from __future__ import annotations
@@ -89,6 +95,33 @@ def _rel(a, b):
     return abs(a - b) / abs(b) if b != 0 else abs(a - b)
 
 
+def configs(G: float = -5.0, rho_l: float = 2.0, rho_g: float = 0.15, max_steps: int = 50_000) -> dict:
+    """The 32^3 and 128^3 plain-method workloads (psi = 1 - exp(-n), E4, tau = 1, the literal
+    initial densities 2.0 / 0.15, unit interface width)."""
+    keys = ("R_e", "dP", "R_s", "sigma_s", "n_in", "n_out", "mass", "max_u", "status_bits")
+    out = {"G": G, "rho_l": rho_l, "rho_g": rho_g, "runs": []}
+    lat = Lattice(32, 32, 32, G=G, prec="f64")
+    try:
+        lat.init_drop((16, 16, 16), 8.0, rho_l, rho_g)
+        _sync()
+        t0 = time.perf_counter()
+        lat.step(2000)
+        o = lat.observables().as_dict()
+        _sync()
+        wall = time.perf_counter() - t0
+        out["runs"].append({"box": 32, "kind": "droplet", "R": 8.0, "prec": "f64", "steps": 2000,
+                            "wall_s": wall, **{k: o[k] for k in keys}})
+    finally:
+        lat.close()
+    for prec in ("f64", "f32"):
+        for kind, (a, b) in (("droplet", (rho_l, rho_g)), ("bubble", (rho_g, rho_l))):
+            st, o, _, wall = _run_droplet(128, 32.0, a, b, prec, G, max_steps=max_steps)
+            out["runs"].append({"box": 128, "kind": kind, "R": 32.0, "prec": prec, "status": st,
+                                "steps": o["steps"], "criterion": o["criterion"], "wall_s": wall,
+                                "MLUPS": o["steps"] * 128 ** 3 / wall / 1e6, **{k: o[k] for k in keys}})
+    return out
+
+
 def precision(L: int | None = 192, radii=(12.0, 24.0, 48.0), G: float = -5.0, precs=("f32", "f16"),
               max_steps: int = 50_000, per_R: float | None = None) -> dict:
     """Errors of the reduced-precision storages against FP64, per radius; the box is
@@ -148,16 +181,20 @@ def main(argv=None):
     p1.add_argument("--radii", default="12,24,48")
     p1.add_argument("--G", type=float, default=-5.0)
     p1.add_argument("--max-steps", type=int, default=50_000)
+    p0 = sub.add_parser("configs")
+    p0.add_argument("--max-steps", type=int, default=50_000)
     p2 = sub.add_parser("eos")
     p2.add_argument("--L", type=int, default=256)
     p2.add_argument("--R", type=float, default=48.0)
     p2.add_argument("--T-fracs", default="0.7,0.8,0.9")
     p2.add_argument("--stencils", default="E6,E8")
     p2.add_argument("--max-steps", type=int, default=50_000)
-    for p in (p1, p2):
+    for p in (p0, p1, p2):
         p.add_argument("--out", default="")
     a = ap.parse_args(argv)
-    if a.study == "precision":
+    if a.study == "configs":
+        res = configs(max_steps=a.max_steps)
+    elif a.study == "precision":
         res = precision(a.L, tuple(float(r) for r in a.radii.split(",")), a.G, max_steps=a.max_steps,
                         per_R=a.per_R or None)
     else:
