@@ -78,16 +78,30 @@ struct StepShape {
   static constexpr size_t smem_bytes = ring_bytes + pops_bytes;
 };
 
-// sum of the 19 populations of a node as a balanced tree (short dependency
-// chains; the order is fixed so every kernel forms bitwise the same density)
+// Mirror-exact summation.  The box, the droplet and its initial profile are
+// symmetric under the three reflections x -> -x, y -> -y, z -> -z about the centre
+// node, and so is the exact dynamics; floating-point sums keep that symmetry only
+// if each reflection maps every sum onto the same operations.  A reflection
+// permutes the populations (x: 1<->2, 7<->10, 8<->9, 11<->14, 12<->13; y: 3<->4,
+// 7<->9, 8<->10, 15<->18, 16<->17; z: 5<->6, 11<->13, 12<->14, 15<->17, 16<->18), so
+// the sums below add opposite pairs first and then exactly the pair sums a
+// reflection swaps; a + b = b + a and a - b = -(b - a) hold exactly, so a mirrored
+// state gives bitwise mirrored densities, momenta and forces, the drop's centre of
+// mass stays on the centre node, and rounding (FP16 storage above all) cannot push
+// the drop off it.
+//
+// sum of the nine opposite-pair sums g_i + g_ibar, grouped by the reflections
+template <typename T>
+__device__ __forceinline__ T pair_sum9(T p12, T p34, T p56, T p78, T p910, T p1112, T p1314, T p1516, T p1718) {
+  return ((p12 + p34) + p56) + (((p78 + p910) + (p1112 + p1314)) + (p1516 + p1718));
+}
+
+// density: rest population plus the mirror-exact sum of the pair sums (the order
+// is fixed, so every kernel forms bitwise the same density)
 template <typename T>
 __device__ __forceinline__ T sum19(const T* v) {
-  const T a = (v[0] + v[1]) + (v[2] + v[3]);
-  const T b = (v[4] + v[5]) + (v[6] + v[7]);
-  const T c = (v[8] + v[9]) + (v[10] + v[11]);
-  const T d = (v[12] + v[13]) + (v[14] + v[15]);
-  const T e = (v[16] + v[17]) + v[18];
-  return ((a + b) + (c + d)) + e;
+  return v[0] + pair_sum9<T>(v[1] + v[2], v[3] + v[4], v[5] + v[6], v[7] + v[8], v[9] + v[10],
+                             v[11] + v[12], v[13] + v[14], v[15] + v[16], v[17] + v[18]);
 }
 
 // Pull the 19 populations of every node of one padded plane (tile + R halo),
@@ -131,46 +145,80 @@ __device__ __forceinline__ void load_plane(const LatticeDesc& d, int x0, int y0,
 
 // Shan-Chen force (Eq. (8)) from psi planes in shared memory.  planes[dz + R]
 // points at the node's own position in the psi plane at offset dz; rows are PX
-// apart.  The stencil is summed in antisymmetric pairs, W (psi(x + xi) -
-// psi(x - xi)) xi, so that the two psi values cancel before they are scaled:
-// a uniform region gives exactly F = 0 and the rounding error scales with F,
-// not with the psi values.  (Summing the 18 terms one by one in raster order
-// lets FP32 rounding build a spurious force that grows the density error of a
-// 1000-step droplet run tenfold.)
+// apart.  The stencil is summed through the differences D(xi) = psi(x + xi) -
+// psi(x - xi), so that two psi values cancel before they are scaled: a uniform
+// region gives exactly F = 0 and the rounding error scales with F, not with the
+// psi values.  (Summing the 18 terms one by one in raster order lets FP32 rounding
+// build a spurious force that grows the density error of a 1000-step droplet run
+// tenfold.)
+// Mirror-exact order: component a of the force is, per shell, a sum over the
+// orbits of the stencil vectors with xi_a > 0 under the two reflections that
+// leave axis a alone -- {(xi_a, +-b, +-c)} -- each orbit summed as
+// ((D(a,b,c) + D(a,-b,c)) + (D(a,b,-c) + D(a,-b,-c))); the shells are then
+// weighted and added in a fixed order.  A reflection of the field maps every
+// orbit sum onto itself (reordered by exactly commuting additions) or onto its
+// negative, so mirrored psi gives a bitwise mirrored force (see sum19).
 // OWN: own[dz + R] holds psi of the node's own column at offset dz (the caller
-// formed those values and kept them in registers); the centre and the pairs
-// along z take them from there instead of from shared memory.  Same values,
-// same order of operations.
+// formed those values and kept them in registers); differences along the node's
+// own column take them from there instead of from shared memory.
+template <typename T, int ST, int PX, bool OWN>
+__device__ __forceinline__ T sc_diff(const T* const* planes, const T* own, int dx, int dy, int dz) {
+  constexpr int R = stencil_radius<ST>();
+  if (OWN && dx == 0 && dy == 0) return own[R + dz] - own[R - dz];
+  return planes[R + dz][dy * PX + dx] - planes[R - dz][-dy * PX - dx];
+}
+
+template <typename T, int ST, int PX, bool OWN>
+__device__ __forceinline__ T sc_force_axis(const T* const* planes, const T* own, int axis) {
+  constexpr int R = stencil_radius<ST>();
+  T F = (T)0;
+  bool any_shell = false;
+#pragma unroll
+  for (int sh = 1; sh <= 3 * R * R; ++sh) {
+    const double W = shell_weight<ST>(sh);
+    if (W == 0.0) continue;
+    T S = (T)0;
+    bool any = false;
+#pragma unroll
+    for (int a = 1; a <= R; ++a) {
+#pragma unroll
+      for (int b = 0; b <= R; ++b) {
+#pragma unroll
+        for (int c = 0; c <= R; ++c) {
+          if (a * a + b * b + c * c != sh) continue;
+          // the vector (a, b, c) in the frame of `axis`: a along it, b and c along the
+          // other two axes in increasing order
+          auto D = [&](int bb, int cc) {
+            return axis == 0 ? sc_diff<T, ST, PX, OWN>(planes, own, a, bb, cc)
+                 : axis == 1 ? sc_diff<T, ST, PX, OWN>(planes, own, bb, a, cc)
+                             : sc_diff<T, ST, PX, OWN>(planes, own, bb, cc, a);
+          };
+          T O;
+          if (b > 0 && c > 0) O = (D(b, c) + D(-b, c)) + (D(b, -c) + D(-b, -c));
+          else if (b > 0) O = D(b, 0) + D(-b, 0);
+          else if (c > 0) O = D(0, c) + D(0, -c);
+          else O = D(0, 0);
+          if (a != 1) O = (T)a * O;
+          S = any ? S + O : O;
+          any = true;
+        }
+      }
+    }
+    if (!any) continue;
+    F = any_shell ? F + (T)W * S : (T)W * S;
+    any_shell = true;
+  }
+  return F;
+}
+
 template <typename T, int ST, int PX, bool OWN = false>
 __device__ __forceinline__ void sc_force_pairs(const T* const* planes, T G, T& Fx, T& Fy, T& Fz,
                                                const T* own = nullptr) {
   constexpr int R = stencil_radius<ST>();
-  T sx = 0, sy = 0, sz = 0;
-#pragma unroll
-  for (int dz = 0; dz <= R; ++dz) {
-#pragma unroll
-    for (int dy = -R; dy <= R; ++dy) {
-#pragma unroll
-      for (int dx = -R; dx <= R; ++dx) {
-        // one representative per pair: dz > 0, or dz == 0 and (dy > 0 or (dy == 0 and dx > 0))
-        const bool upper = dz > 0 || (dz == 0 && (dy > 0 || (dy == 0 && dx > 0)));
-        const double Wd = shell_weight<ST>(dx * dx + dy * dy + dz * dz);
-        if (upper && Wd != 0.0) {
-          const T d = (OWN && dx == 0 && dy == 0)
-                          ? own[R + dz] - own[R - dz]
-                          : planes[R + dz][dy * PX + dx] - planes[R - dz][-dy * PX - dx];
-          const T Wdiff = (T)Wd * d;
-          if (dx != 0) sx += (T)dx * Wdiff;
-          if (dy != 0) sy += (T)dy * Wdiff;
-          if (dz != 0) sz += (T)dz * Wdiff;
-        }
-      }
-    }
-  }
   const T k = -G * (T)(1.0 / 3.0) * (OWN ? own[R] : planes[R][0]);
-  Fx = k * sx;
-  Fy = k * sy;
-  Fz = k * sz;
+  Fx = k * sc_force_axis<T, ST, PX, OWN>(planes, own, 0);
+  Fy = k * sc_force_axis<T, ST, PX, OWN>(planes, own, 1);
+  Fz = k * sc_force_axis<T, ST, PX, OWN>(planes, own, 2);
 }
 
 // Force at interior node (tx, ty) of the current plane from the psi ring;
@@ -227,12 +275,37 @@ __device__ __forceinline__ void collide(T* g, T dn, T n, T ux, T uy, T uz, T Fx,
     }
   }
   if (CLOSE_MASS) {
-    // pair sums first (their odd parts cancel), then a balanced tree
-    const T p1 = g[1] + g[2], p2 = g[3] + g[4], p3 = g[5] + g[6];
-    const T p4 = g[7] + g[8], p5 = g[9] + g[10], p6 = g[11] + g[12];
-    const T p7 = g[13] + g[14], p8 = g[15] + g[16], p9 = g[17] + g[18];
-    g[0] = dn - ((((p1 + p2) + (p3 + p4)) + ((p5 + p6) + (p7 + p8))) + p9);
+    // pair sums first (their odd parts cancel), then the mirror-exact grouping
+    g[0] = dn - pair_sum9<T>(g[1] + g[2], g[3] + g[4], g[5] + g[6], g[7] + g[8], g[9] + g[10], g[11] + g[12],
+                             g[13] + g[14], g[15] + g[16], g[17] + g[18]);
   }
+}
+
+// The unit-tau collision of `collide<T, true, true>` with each post-collision
+// population stored as soon as it is formed (store(i, g_i)): only the nine pair
+// sums stay live for the mass closure, not all nineteen values.  Same operations
+// in the same order, so the stored values are bitwise those of collide().
+template <typename T, typename Store>
+__device__ __forceinline__ void collide_unit_tau_store(T dn, T n, T ux, T uy, T uz, T Fx, T Fy, T Fz,
+                                                       Store store) {
+  const T uu = ux * ux + uy * uy + uz * uz;
+  const T uF = ux * Fx + uy * Fy + uz * Fz;
+  const T cg = (T)1 - (T)0.5 * (T)1;
+  const T base = (T)1 * (dn - (T)1.5 * n * uu) - (T)3 * cg * uF;
+  T p[9];
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    const T eu = (T)cx(i) * ux + (T)cy(i) * uy + (T)cz(i) * uz;
+    const T eF = (T)cx(i) * Fx + (T)cy(i) * Fy + (T)cz(i) * Fz;
+    const T wi = (T)wq(i);
+    const T even = base + (T)1 * (T)4.5 * n * eu * eu + (T)9 * cg * eu * eF;
+    const T odd = (T)3 * ((T)1 * n * eu + cg * eF);
+    const T ga = wi * (even + odd), gb = wi * (even - odd);
+    store(i, ga);
+    store(i + 1, gb);
+    p[i / 2] = ga + gb;
+  }
+  store(0, dn - pair_sum9<T>(p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7], p[8]));
 }
 
 // density and momentum of one node: momentum from the differences of the nine
@@ -243,10 +316,11 @@ __device__ __forceinline__ void moments(const T* g, T& dn, T& jx, T& jy, T& jz) 
   const T d12 = g[1] - g[2], d34 = g[3] - g[4], d56 = g[5] - g[6];
   const T d78 = g[7] - g[8], d910 = g[9] - g[10], d1112 = g[11] - g[12];
   const T d1314 = g[13] - g[14], d1516 = g[15] - g[16], d1718 = g[17] - g[18];
-  // x: 1 (+), 7 (+), 9 (+), 11 (+), 13 (+); y: 3, 7, 10, 15, 17 (+); z: 5, 11, 14, 15, 18 (+)
-  jx = (d12 + d78) + (d910 + (d1112 + d1314));
-  jy = (d34 + d78) + ((d1516 + d1718) - d910);
-  jz = (d56 + d1112) + ((d1516 - d1718) - d1314);
+  // x: 1 (+), 7 (+), 9 (+), 11 (+), 13 (+); y: 3, 7, 10, 15, 17 (+); z: 5, 11, 14, 15, 18 (+);
+  // the differences a reflection swaps are added (or subtracted) first: mirror-exact
+  jx = (d12 + (d78 + d910)) + (d1112 + d1314);
+  jy = (d34 + (d78 - d910)) + (d1516 + d1718);
+  jz = (d56 + (d1112 - d1314)) + (d1516 - d1718);
 }
 
 template <typename T>
