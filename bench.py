@@ -57,14 +57,21 @@ def measured_peak_gbs():
 
 
 KERNEL_SOURCES = ("lbm_common.cuh", "lbm_kernels.cuh", "lbm_kernels_async.cuh", "lbm_kernels_chunk.cuh",
-                  "lbm_kernels_moment.cuh", "lbm_lattice_inst.cuh")
+                  "lbm_kernels_moment.cuh", "lbm_kernels_tma.cuh", "lbm_lattice_inst.cuh")
 
 
-def measured_traffic(prec):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary, or None
-    when there is none for this precision or the kernel sources changed since."""
+PROFILE_STEMS = {7: "lattice_tma", 6: "lattice_moment_elem", 5: "lattice_moment"}
+
+
+def measured_traffic(prec, kind=5):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary of the
+    128^3 workload, or None when there is none for this kernel and precision or the
+    kernel sources changed since."""
     import hashlib
-    summary = ROOT / "profiles" / f"lattice_moment_{prec}_128.md"
+    stem = PROFILE_STEMS.get(int(kind))
+    if stem is None:
+        return None
+    summary = ROOT / "profiles" / f"{stem}_{prec}_128.md"
     if not summary.exists():
         return None
     fields = {}
@@ -77,6 +84,19 @@ def measured_traffic(prec):
     if fields.get("source_sha256") != h or "traffic_bytes_per_launch" not in fields:
         return None
     return int(fields["traffic_bytes_per_launch"])
+
+
+KERNEL_KINDS = {
+    7: "lattice_tma_kernel (TMA tensor-tile pull + on-chip psi halo + SC force + Guo-BGK at tau = 1 + store)",
+    6: "lattice_moment_kernel, element copies (pull + on-chip psi halo + SC force + Guo-BGK at tau = 1 + store)",
+    5: "lattice_moment_kernel, row chunks (pull + on-chip psi halo + SC force + Guo-BGK at tau = 1 + store)",
+    4: "lattice_chunk_kernel", 1: "lattice_async_kernel", 0: "lattice_kernel",
+}
+
+
+def kernel_name(tile_code):
+    """The fused step kernel a tile code selects (kind = code / 10^8)."""
+    return "fused step, " + KERNEL_KINDS.get(int(tile_code) // 100000000, f"kind {int(tile_code) // 100000000}")
 
 
 class ClockSampler:
@@ -430,7 +450,7 @@ def main():
     avg_launch_s = kern_ms * 1e-3 / n_launch
     bytes_per_launch = BYTES_PER_LU[args.prec] * N
     achieved = bytes_per_launch / avg_launch_s / 1e9
-    traffic = measured_traffic(args.prec)
+    traffic = measured_traffic(args.prec, lats[0].get_tile() // 100000000)
 
     # end to end through the public API with host buffers
     host = []
@@ -516,8 +536,7 @@ def main():
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                     "kernel": "fused step, lattice_moment_kernel (pull + on-chip psi halo + SC force "
-                               "+ Guo-BGK at tau = 1 + store)",
+                     "kernel": kernel_name(lats[0].get_tile()), "tile": lats[0].get_tile(),
                      "bytes_per_launch": bytes_per_launch, "avg_launch_us": avg_launch_s * 1e6},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": len(lats) * N * 8,

@@ -53,6 +53,7 @@ struct lbm_ctx {
   int graph_len;
   lbm_obs last;
   int have_last;
+  TmaMaps tma;                // tensor maps of pop[0] / pop[1] for the TMA step kernel (kind 7)
   char err[512];
 };
 
@@ -162,11 +163,26 @@ LatticeDesc desc_of(const lbm_ctx* c, int src_buf) {
   d.eos.Rgas = c->eos.Rgas;
   d.eos.T = c->eos.T;
   d.err = c->err_dev;
+  d.tma = c->tma.ok ? &c->tma : nullptr;
   return d;
 }
 
-TileCfg default_tile(lbm_box b, int prec, int stencil, double tau) {
+// the TMA kernel (kind 7) as the default where it applies (else it is offered to the
+// autotuner and lbm_set_tile only)
+constexpr bool kTmaDefault = false;
+
+TileCfg default_tile(lbm_box b, int prec, int stencil, double tau, bool allow_tma = true) {
   TileCfg t;
+  // FP32 E4 at tau = 1 on boxes the TMA kernel takes: the moment kernel fed by
+  // tensor-tile copies (kind 7)
+  if (kTmaDefault && allow_tma && prec == kF32 && stencil == 4 && tau == 1.0 && tma_box_ok(b.nx, b.ny, b.nz, 8)) {
+    t.kind = 7;
+    t.bx = 32;
+    t.by = 8;
+    t.zchunk = 0;
+    t.depth = 1;
+    return t;
+  }
   t.zchunk = b.nz < 16 ? b.nz : 16;
   t.bx = 32;
   t.by = stencil == 4 ? 8 : 4;
@@ -226,6 +242,28 @@ TileCfg default_tile(lbm_box b, int prec, int stencil, double tau) {
   return t;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
 long long tile_code(const TileCfg& t) {
   return (long long)t.kind * 100000000 + (long long)t.bx * 1000000 + t.by * 10000 +
          (t.kind >= 1 ? t.zchunk * 10 + t.depth : t.zchunk);
@@ -255,18 +293,12 @@ std::vector<TileCfg> step_candidates(const lbm_ctx* c) {
   }
   if (c->prec != kF16) {
     const int R = radius_of(c->stencil);
-    const int (*bs)[3] = c->stencil == 4 ? kBulkE4 : kBulkWide;
-    const int nb = c->stencil == 4 ? kNumBulkE4 : kNumBulkWide;
-    for (int k = 0; k < nb; ++k) {
-      // rows must be 16-byte aligned and wrap at most once
-      if (c->box.nx % 4 != 0 || c->box.nx < bs[k][0] + 8) continue;
-      if (bulk_smem_bytes(storage_bytes(c->prec), R, bs[k][0], bs[k][1], bs[k][2]) > kMaxSmemPerCta)
-        continue;
+    if (c->tma.ok) {   // kind 7: the moment kernel fed by TMA tensor-tile copies
       for (int zc : {0, 8, 16, 32}) {
         if (zc > c->box.nz) continue;
-        TileCfg t{bs[k][0], bs[k][1], zc};
-        t.kind = 2;
-        t.depth = bs[k][2];
+        TileCfg t{c->tma.bx, c->tma.by, zc};
+        t.kind = 7;
+        t.depth = 1;
         out.push_back(t);
       }
     }
@@ -537,6 +569,9 @@ lbm_status lbm_create(lbm_box box, double tau, double G, lbm_eos eos, int stenci
   c->n0 = 0.0;
   c->scale = 1.0;
   c->step_cfg = default_tile(box, prec, stencil, tau);
+  if (prec == kF32 && stencil == 4 && tau == 1.0 && tma_box_ok(box.nx, box.ny, box.nz, 8))
+    build_tma_maps(&c->tma, c->pop[0], c->pop[1], box.nx, box.ny, box.nz, 1, 32, 8);
+  if (!c->tma.ok && c->step_cfg.kind == 7) c->step_cfg = default_tile(box, prec, stencil, tau, false);
   c->obs_zchunk = default_obs_zchunk(box);
   c->graph[0] = c->graph[1] = nullptr;
   c->graph_len = 128;
@@ -1735,3 +1770,35 @@ lbm_status lbm_group_step(lbm_group* g, long long n) {
 }
 
 const char* lbm_group_last_error(const lbm_group* g) { return g ? g->err : g_err; }
+
+// ---------------------------------------------------------------- TMA tensor maps
+
+bool lbm::build_tma_maps(TmaMaps* t, const void* pop0, const void* pop1, int nx, int ny, int nz, int R,
+                         int bx, int by) {
+  t->ok = 0;
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc || !tma_box_ok(nx, ny, nz, by) || R < 1 || R + 3 > kMaxTmaMaps) return false;
+  const int XW = bx + 8, PY = by + 2 * R;   // the kernel's boxes (TmaShape)
+  const cuuint64_t N = (cuuint64_t)nx * ny * nz;
+  const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)Q};
+  const cuuint64_t strides[3] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4, N * 4};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const void* base[2] = {pop0, pop1};
+  for (int b = 0; b < 2; ++b) {
+    if (((uintptr_t)base[b] & 15) != 0) return false;
+    for (int k = 0; k <= R + 2; ++k) {
+      // k = 0: the stage box; 1 .. R + 1: k wrapped rows; R + 2: the 16-byte x apron
+      const cuuint32_t box[4] = {(cuuint32_t)(k == R + 2 ? 4 : XW), (cuuint32_t)(k == 0 || k == R + 2 ? PY : k), 1,
+                                 1};
+      const CUresult r = enc(&t->map[b][k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base[b]), dims,
+                             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return false;
+    }
+    t->base[b] = base[b];
+  }
+  t->bx = bx;
+  t->by = by;
+  t->ok = 1;
+  return true;
+}

@@ -36,9 +36,9 @@ __host__ __device__ constexpr unsigned long long pack_component(int axis) {
   }
   return p;
 }
-__host__ __device__ __forceinline__ int cx_rt(int i) { return (int)((pack_component(0) >> (2 * i)) & 3ull) - 1; }
-__host__ __device__ __forceinline__ int cy_rt(int i) { return (int)((pack_component(1) >> (2 * i)) & 3ull) - 1; }
-__host__ __device__ __forceinline__ int cz_rt(int i) { return (int)((pack_component(2) >> (2 * i)) & 3ull) - 1; }
+__host__ __device__ constexpr int cx_rt(int i) { return (int)((pack_component(0) >> (2 * i)) & 3ull) - 1; }
+__host__ __device__ constexpr int cy_rt(int i) { return (int)((pack_component(1) >> (2 * i)) & 3ull) - 1; }
+__host__ __device__ constexpr int cz_rt(int i) { return (int)((pack_component(2) >> (2 * i)) & 3ull) - 1; }
 
 // D3Q19 weights: 1/3 rest, 1/18 axis, 1/36 diagonal
 __host__ __device__ constexpr double wq(int i) {
@@ -128,7 +128,10 @@ struct LatticeDesc {
   double scale;         // storage scale (1 for F64/F32)
   EosParams eos;
   int* err;             // device flag set by a kernel whose bounded wait ran out (may be null)
+  const void* tma;      // host: the lattice's TMA tensor maps (TmaMaps) or null; kernels ignore it
 };
+
+constexpr int kMaxTmaMaps = 4;   // tensor maps per population buffer (TMA step kernel)
 
 __host__ __device__ __forceinline__ int wrap(int g, int n) {
   return g < 0 ? g + n : (g >= n ? g - n : g);

@@ -3,7 +3,7 @@
 // Same pipeline and arithmetic as lattice_async_kernel; the copies differ.
 // Instead of one 4- or 8-byte cp.async per pulled population and padded node,
 // a stage row of population i holds the 16-byte aligned x range
-// [x0 - 4, x0 + BX + 4) of the source row (the row-bulk kernel's layout), filled
+// [x0 - 4, x0 + BX + 4) of the source row, filled
 // by 16-byte cp.async.cg copies (L2 only, no L1 allocation).  Because nx is a
 // multiple of 4, every 16-byte chunk lies wholly inside the row or wholly in its
 // periodic image, so a chunk wraps as a unit.  The pull shift in x becomes an
@@ -15,9 +15,10 @@
 #pragma once
 
 #include "lbm_kernels_async.cuh"
-#include "lbm_kernels_bulk.cuh"
 
 namespace lbm {
+
+constexpr int kChunkApron = 4;   // staged elements left of the tile (one 16-byte FP32 chunk)
 
 template <int P, int ST, int BX, int BY, int D>
 struct ChunkShape {
@@ -27,7 +28,7 @@ struct ChunkShape {
   static constexpr int PY = BY + 2 * R;
   static constexpr int NPAD = PX * PY;
   static constexpr int NT = BX * BY;
-  static constexpr int XW = BX + 2 * kBulkApron;       // staged row width
+  static constexpr int XW = BX + 2 * kChunkApron;       // staged row width
   static constexpr int VE = 16 / (int)sizeof(T);       // elements per chunk
   static constexpr int NCH = XW / VE;                  // chunks per staged row
   static constexpr int NS = R + 1 + D;
@@ -36,7 +37,7 @@ struct ChunkShape {
   static constexpr size_t stage_elems = (size_t)Q * PY * XW;
   static constexpr size_t smem_bytes = sizeof(T) * (NS * stage_elems + NR * NPAD);
   static_assert(XW % VE == 0, "staged rows are whole chunks");
-  static_assert(R + 1 <= kBulkApron, "apron must cover the pull of the halo");
+  static_assert(R + 1 <= kChunkApron, "apron must cover the pull of the halo");
 };
 
 __device__ __forceinline__ void cp_async_chunk16(void* smem, const void* gmem) {
@@ -74,7 +75,7 @@ __device__ __forceinline__ void chunk_process_item(const LatticeDesc& d, int zch
   const int w = min(BX, nx - x0), h = min(BY, ny - y0);
   const bool active = tx < w && ty < h;
   const int rows = h + 2 * R;
-  const int xa = x0 - kBulkApron;
+  const int xa = x0 - kChunkApron;
 
   // copy positions: a position is one 16-byte chunk (staged row jy, chunk k) of a
   // stage; a thread copies its position for a fixed range of populations, so
@@ -152,7 +153,7 @@ __device__ __forceinline__ void chunk_process_item(const LatticeDesc& d, int zch
         if (!valid[s]) continue;
         const int j = tid + s * NT;
         const int jx = j % PX, jy = j / PX;
-        const T* row0 = st + jy * XW + jx + kBulkApron - R;
+        const T* row0 = st + jy * XW + jx + kChunkApron - R;
         T v[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) v[i] = row0[i * PY * XW - cx(i)];
@@ -165,7 +166,7 @@ __device__ __forceinline__ void chunk_process_item(const LatticeDesc& d, int zch
     if (k >= 0 && active) {
       const T* st = stages + (qc % NS) * Sh::stage_elems;
       const int jc = (ty + R) * PX + (tx + R);
-      const T* row0 = st + (ty + R) * XW + tx + kBulkApron;
+      const T* row0 = st + (ty + R) * XW + tx + kChunkApron;
       T g[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) g[i] = row0[i * PY * XW - cx(i)];

@@ -42,7 +42,7 @@ struct MomentShape {
   static constexpr int NHPER = (NH + NT - 1) / NT;     // halo nodes per thread
   using S = typename Storage<P>::S;                    // stored (and staged) type
   static constexpr int VE = 16 / (int)sizeof(S);       // elements per 16-byte chunk
-  static constexpr int APRON = VE > kBulkApron ? VE : kBulkApron;   // staged left of the tile
+  static constexpr int APRON = VE > kChunkApron ? VE : kChunkApron;   // staged left of the tile
   static constexpr int XW = BX + 2 * APRON;
   static constexpr int NCH = XW / VE;
   static constexpr int NS = 1 + D;
@@ -77,6 +77,26 @@ __device__ __forceinline__ int halo_node(int h) {
   h -= R * PX;
   const int row = R + h / (2 * R), c = h % (2 * R);
   return row * PX + (c < R ? c : PX - 2 * R + c);
+}
+
+// the same ring in warp-row order, for 32-wide tiles with R = 1: the first 32
+// nodes of the top halo row, the first 32 of the bottom row, the two remaining
+// nodes of each, then the side columns row by row -- each of the first two warps
+// reads one contiguous row (no bank conflicts there)
+template <int BX, int BY, int R>
+__device__ __forceinline__ int halo_node_rows(int h) {
+  static_assert(BX == 32 && R == 1, "warp-row order is defined for 32-wide tiles and R = 1");
+  constexpr int PX = BX + 2 * R, PY = BY + 2 * R;
+  if (h < 32) return h;
+  h -= 32;
+  if (h < 32) return (PY - 1) * PX + h;
+  h -= 32;
+  if (h < PX - 32) return 32 + h;
+  h -= PX - 32;
+  if (h < PX - 32) return (PY - 1) * PX + 32 + h;
+  h -= PX - 32;
+  const int row = 1 + h / 2, c = h % 2;
+  return row * PX + (c == 0 ? 0 : PX - 1);
 }
 
 template <int P, int ST, int BX, int BY, int D, bool ELEM = false>

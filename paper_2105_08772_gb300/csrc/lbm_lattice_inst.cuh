@@ -2,9 +2,9 @@
 // lbm_lattice_<prec>.cu includes this file for its own storage precision.
 #pragma once
 
-#include "lbm_kernels_bulk.cuh"
 #include "lbm_kernels_chunk.cuh"
 #include "lbm_kernels_moment.cuh"
+#include "lbm_kernels_tma.cuh"
 #include "lbm_launch.h"
 
 namespace lbm {
@@ -72,27 +72,6 @@ static cudaError_t launch_async_variant(const LatticeDesc& d, int zchunk, bool p
     cudaError_t e = prepare_persistent(kern, Sh::NT, Sh::smem_bytes, &resident);
     if (e != cudaSuccess || prepare) return e;
   }
-  const long long cols = (long long)((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
-  const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
-  const long long items = cols * ((d.nz + zc - 1) / zc);
-  const long long grid = items < resident ? items : resident;
-  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, zc);
-  return cudaGetLastError();
-}
-
-template <int P, int ST, int BX, int BY, int D, bool UNIT_TAU>
-static cudaError_t launch_bulk_variant(const LatticeDesc& d, int zchunk, bool prepare,
-                                       cudaStream_t s) {
-  using Sh = BulkShape<P, ST, BX, BY, D>;
-  static_assert(Sh::smem_bytes == bulk_smem_bytes(sizeof(typename Sh::T), Sh::R, BX, BY, D),
-                "host and device disagree on the bulk kernel's shared memory");
-  auto kern = lattice_bulk_kernel<P, ST, BX, BY, D, UNIT_TAU>;
-  static int resident = 0;
-  if (prepare || resident == 0) {
-    cudaError_t e = prepare_persistent(kern, Sh::NT, Sh::smem_bytes, &resident);
-    if (e != cudaSuccess || prepare) return e;
-  }
-  if (d.nx % 4 != 0 || d.nx < Sh::XW) return cudaErrorInvalidValue;
   const long long cols = (long long)((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
   const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
   const long long items = cols * ((d.nz + zc - 1) / zc);
@@ -201,17 +180,6 @@ static cudaError_t dispatch_chunk(const LatticeDesc& d, TileCfg c, cudaStream_t 
     }
     return cudaErrorInvalidValue;
   }
-}
-
-template <int P, int ST, int BX, int BY, int D>
-static cudaError_t launch_bulk(const LatticeDesc& d, int zchunk, bool prepare, cudaStream_t s) {
-  if (prepare) {
-    cudaError_t e = launch_bulk_variant<P, ST, BX, BY, D, true>(d, 0, true, s);
-    if (e != cudaSuccess) return e;
-    return launch_bulk_variant<P, ST, BX, BY, D, false>(d, 0, true, s);
-  }
-  if (d.omega == 1.0) return launch_bulk_variant<P, ST, BX, BY, D, true>(d, zchunk, false, s);
-  return launch_bulk_variant<P, ST, BX, BY, D, false>(d, zchunk, false, s);
 }
 
 // Pipelined step kernel on a persistent grid of (resident CTAs per SM) x SMs;
@@ -380,22 +348,38 @@ static cudaError_t dispatch_batch_stencil(int stencil, int mode, const BatchEntr
   return cudaErrorInvalidValue;
 }
 
-template <int P, int ST>
-static cudaError_t dispatch_bulk(const LatticeDesc& d, TileCfg c, cudaStream_t s) {
-  if constexpr (P == kF16) {
-    return cudaErrorInvalidValue;
-  } else {
-    const bool prep = c.prepare;
-    if (ST == 4) {
-      if (c.bx == 32 && c.by == 8 && c.depth == 1) return launch_bulk<P, 4, 32, 8, 1>(d, c.zchunk, prep, s);
-      if (c.bx == 32 && c.by == 4 && c.depth == 1) return launch_bulk<P, 4, 32, 4, 1>(d, c.zchunk, prep, s);
-      if (c.bx == 64 && c.by == 4 && c.depth == 1) return launch_bulk<P, 4, 64, 4, 1>(d, c.zchunk, prep, s);
-      if (c.bx == 32 && c.by == 8 && c.depth == 2) return launch_bulk<P, 4, 32, 8, 2>(d, c.zchunk, prep, s);
-    } else {
-      if (c.bx == 32 && c.by == 4 && c.depth == 1) return launch_bulk<P, ST, 32, 4, 1>(d, c.zchunk, prep, s);
-    }
-    return cudaErrorInvalidValue;
+// the unit-tau moment kernel fed by TMA tensor-tile copies (kind 7; FP32 storage,
+// tau = 1, the box rules of tma_box_ok, tensor maps encoded for this tile)
+template <int ST, int BX, int BY>
+static cudaError_t launch_tma(const LatticeDesc& d, int zchunk, bool prepare, cudaStream_t s) {
+  using Sh = TmaShape<ST, BX, BY>;
+  auto kern = lattice_tma_kernel<ST, BX, BY>;
+  static int resident = 0;
+  if (prepare || resident == 0) {
+    cudaError_t e = prepare_persistent(kern, Sh::NT, Sh::smem_bytes, &resident);
+    if (e != cudaSuccess || prepare) return e;
   }
+  const TmaMaps* tm = static_cast<const TmaMaps*>(d.tma);
+  if (!tm || !tm->ok || tm->bx != BX || tm->by != BY || d.omega != 1.0) return cudaErrorInvalidValue;
+  if (!tma_box_ok(d.nx, d.ny, d.nz, BY)) return cudaErrorInvalidValue;
+  const int b = d.src == tm->base[0] ? 0 : (d.src == tm->base[1] ? 1 : -1);
+  if (b < 0) return cudaErrorInvalidValue;
+  TmaMapSet maps;
+  for (int k = 0; k < kMaxTmaMaps; ++k) maps.map[k] = tm->map[b][k];
+  const long long cols = (long long)((d.nx + BX - 1) / BX) * (d.ny / BY);
+  const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
+  const long long items = cols * ((d.nz + zc - 1) / zc);
+  const long long grid = items < resident ? items : resident;
+  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, maps, zc);
+  return cudaGetLastError();
+}
+
+template <int P, int ST>
+static cudaError_t dispatch_tma(const LatticeDesc& d, TileCfg c, cudaStream_t s) {
+  if constexpr (P == kF32 && ST == 4) {
+    if (c.bx == 32 && c.by == 8 && c.depth == 1) return launch_tma<4, 32, 8>(d, c.zchunk, c.prepare, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <int P, int ST, int MODE>
@@ -412,10 +396,8 @@ template <int P>
 static cudaError_t dispatch_lattice(int stencil, int mode, const LatticeDesc& d, TileCfg c,
                                     const ObsArgs& oa, cudaStream_t s) {
   if (c.zchunk < 0) return cudaErrorInvalidValue;
-  if (mode == kModeStep && c.kind == 2) {
-    if (stencil == 4) return dispatch_bulk<P, 4>(d, c, s);
-    if (stencil == 6) return dispatch_bulk<P, 6>(d, c, s);
-    if (stencil == 8) return dispatch_bulk<P, 8>(d, c, s);
+  if (mode == kModeStep && c.kind == 7) {
+    if (stencil == 4) return dispatch_tma<P, 4>(d, c, s);
     return cudaErrorInvalidValue;
   }
   if (mode == kModeStep && c.kind == 6) {

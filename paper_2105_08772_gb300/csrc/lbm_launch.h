@@ -2,6 +2,7 @@
 // translation units (one per storage precision).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lbm_common.cuh"
@@ -12,9 +13,9 @@ namespace lbm {
 // Step-kernel configuration.  kind 0: lattice_kernel (register loads), one CTA
 // per (column, chunk of zchunk planes).  kind 1: lattice_async_kernel
 // (cp.async stages, prefetch depth `depth`) on a persistent grid; zchunk 0
-// lets the launcher choose the chunk, > 0 fixes it.  kind 2:
-// lattice_bulk_kernel (row bulk copies), same grid rules; needs nx % 4 == 0
-// and nx >= bx + 8.
+// lets the launcher choose the chunk, > 0 fixes it.  kind 4: lattice_chunk_kernel
+// (16-byte row chunks), kind 5: the unit-tau moment kernel with row chunks, kind 6:
+// the moment kernel with element copies; same grid rules.
 // prepare = true launches nothing: it sets the kernel's shared-memory limit
 // (and caches the occupancy), which must happen outside any stream capture.
 struct TileCfg {
@@ -24,6 +25,25 @@ struct TileCfg {
   bool prepare = false;
 };
 
+// TMA tensor maps of both population buffers of one lattice (host side; kind 7):
+// map[b][0] boxes XW x PY, map[b][k] XW x k wrapped rows (k = 1 .. R + 1),
+// map[b][R + 2] 4 x PY (a 16-byte x apron), over the 4-D view (x, y, z,
+// population) of buffer b
+struct TmaMaps {
+  int ok = 0;
+  int bx = 0, by = 0;               // tile shape the boxes were encoded for
+  const void* base[2] = {nullptr, nullptr};
+  CUtensorMap map[2][kMaxTmaMaps];
+};
+// Encode the maps of one FP32 lattice for bx x by tiles of a stencil of radius R.
+// Returns false (t->ok = 0) when the box or the lattice does not meet the TMA
+// kernel's requirements or the driver's encoder is unavailable or refuses.
+bool build_tma_maps(TmaMaps* t, const void* pop0, const void* pop1, int nx, int ny, int nz, int R, int bx,
+                    int by);
+// the TMA kernel's requirements on the box (kind 7)
+inline bool tma_box_ok(int nx, int ny, int nz, int by) {
+  return nx % 4 == 0 && nx >= 64 && ny % by == 0 && ny >= 2 * by && nz >= 3;
+}
 // tile shapes compiled for the register-load step kernel (E4 / wider stencils)
 constexpr int kNumShapesE4 = 3;
 constexpr int kShapesE4[kNumShapesE4][2] = {{32, 4}, {32, 8}, {64, 4}};
@@ -60,20 +80,6 @@ inline cudaError_t launch_lattice(int prec, int stencil, int mode, const Lattice
 constexpr size_t async_smem_bytes(size_t elem, int R, int bx, int by, int depth) {
   return elem * (size_t)(bx + 2 * R) * (by + 2 * R) * ((R + 1 + depth) * Q + 2 * R + 1);
 }
-// dynamic shared memory of the row-bulk kernel: (R + 1 + depth) stages of
-// 19 x (by + 2R) rows of bx + 8 elements, psi and dn rings of 2R + 1 padded
-// planes, then one 8-byte mbarrier per stage
-constexpr size_t bulk_smem_bytes(size_t elem, int R, int bx, int by, int depth) {
-  return (elem * ((size_t)(R + 1 + depth) * Q * (by + 2 * R) * (bx + 8) +
-                  2 * (size_t)(2 * R + 1) * (bx + 2 * R) * (by + 2 * R)) + 15) / 16 * 16 +
-         8 * (size_t)(R + 1 + depth);
-}
-// (bx, by, depth) compiled for the row-bulk step kernel
-constexpr int kNumBulkE4 = 4;
-constexpr int kBulkE4[kNumBulkE4][3] = {{32, 8, 1}, {32, 4, 1}, {64, 4, 1}, {32, 8, 2}};
-constexpr int kNumBulkWide = 1;
-constexpr int kBulkWide[kNumBulkWide][3] = {{32, 4, 1}};
-
 // dynamic shared memory of the chunked kernel: (R + 1 + depth) stages of
 // 19 x (by + 2R) rows of bx + 8 elements, psi ring of 2R + 1 padded planes
 constexpr size_t chunk_smem_bytes(size_t elem, int R, int bx, int by, int depth) {

@@ -9,6 +9,7 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("box,stencil,prec,tau", [
     ((128, 128, 128), "E4", "f32", 1.0),
+    ((156, 156, 156), "E4", "f32", 1.0),
     ((127, 127, 127), "E4", "f32", 1.0),
     ((40, 40, 40), "E4", "f64", 1.0),
     ((16, 16, 16), "E4", "f64", 0.8),

@@ -281,41 +281,6 @@ def test_full_size_steps_in_bench_configuration(prec):
 
 
 @pytest.mark.parametrize("prec,code", [(p, c) for p in ("f64", "f32")
-                                       for c in (232080001, 232040001, 264040001, 232080081)]
-                         + [("f32", 232080002)])
-def test_row_bulk_kernel_matches_pipelined_kernel_and_oracle(prec, code):
-    """The row-bulk kernel (kind 2) does the pipelined kernel's arithmetic on the same
-    values: bitwise-equal fields; and it matches the oracle.  nx = 72 with 32-wide tiles
-    has a ragged last column whose staged rows wrap at the right end.  (FP64 with
-    prefetch depth 2 does not fit one CTA's shared memory and is not offered.)"""
-    shape = (13, 22, 72)
-    f0 = inputs.random_populations(shape, seed=21)
-    a = lattice(shape, prec=prec)
-    a.set_populations(f0)
-    a.set_tile(code)
-    a.step(130)
-    b = lattice(shape, prec=prec)
-    b.set_populations(f0)
-    b.set_tile(132080001)
-    b.step(130)
-    assert np.array_equal(a.get_populations(), b.get_populations())
-    if prec == "f64":
-        ref = lbm3d.run(f0, oracle_model(), 130)
-        assert np.max(np.abs(a.get_populations() - ref)) < 1e-12
-
-
-def test_row_bulk_kernel_wide_stencil_and_tau():
-    shape = (9, 10, 48)
-    f0 = inputs.random_populations(shape, seed=22)
-    a = lattice(shape, stencil="E6", tau=0.8)
-    a.set_populations(f0)
-    a.set_tile(232040001)
-    a.step(40)
-    ref = lbm3d.run(f0, oracle_model(stencil="E6", tau=0.8), 40)
-    assert np.max(np.abs(a.get_populations() - ref)) < 1e-12
-
-
-@pytest.mark.parametrize("prec,code", [(p, c) for p in ("f64", "f32")
                                        for c in (432080001, 432040001, 464040001, 432080081)]
                          + [("f32", 432080002), ("f32", 432040002)])
 def test_chunked_kernel_matches_pipelined_kernel_and_oracle(prec, code):
@@ -373,6 +338,47 @@ def test_moment_kernel_matches_pipelined_kernel_and_oracle(prec, code, tau):
     if prec == "f64":
         ref = lbm3d.run(f0, oracle_model(tau=tau), 130)
         assert np.max(np.abs(a.get_populations() - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(13, 16, 64), (9, 24, 72), (5, 32, 68), (7, 40, 128), (3, 16, 96)])
+def test_tma_kernel_matches_moment_kernel_and_oracle(shape):
+    """The moment kernel fed by TMA tensor-tile copies (kind 7) stages the same values as
+    the row-chunk kernel (kind 5): bitwise-equal fields after 130 steps, both buffer
+    parities.  The boxes cover every periodic case the tensor boxes and the fix-ups
+    handle: tiles wrapping in x on the left and on the right, in y at the top and the
+    bottom, the four corners, a ragged last column (nx = 72, and nx = 68 with a 4-wide
+    column), the minimum z (nz = 3)."""
+    f0 = inputs.random_populations(shape, seed=31)
+    a = lattice(shape, prec="f32")
+    a.set_tile(732080001)
+    a.set_populations(f0)
+    a.step(130)
+    b = lattice(shape, prec="f32")
+    b.set_populations(f0)
+    b.set_tile(532080001)
+    b.step(130)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    c = lattice(shape, prec="f32")
+    c.set_tile(732080001)
+    c.set_populations(f0)
+    c.step(3)
+    ref = lbm3d.run(f0, oracle_model(), 3)
+    rho_ref = lbm3d.density(ref)
+    assert np.max(np.abs(c.rho() - rho_ref) / rho_ref) < 2e-6
+
+
+def test_tma_kernel_is_offered_only_where_it_applies():
+    """Kind 7 needs tau = 1, FP32 storage and the box rules; elsewhere its tile code is
+    refused and the lattice keeps its kernel."""
+    for kw in ({"tau": 0.8}, {"prec": "f64"}):
+        lat = lattice((8, 16, 64), **kw)
+        before = lat.get_tile()
+        with pytest.raises(P.LBMError):
+            lat.set_tile(732080001)
+        assert lat.get_tile() == before
+    lat = lattice((8, 20, 64), prec="f32")            # ny % 8 != 0
+    with pytest.raises(P.LBMError):
+        lat.set_tile(732080001)
 
 
 @pytest.mark.parametrize("stencil", ["E6", "E8"])

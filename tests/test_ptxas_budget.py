@@ -4,7 +4,9 @@ flags.  Occupancy is what the moment kernels are designed around:
   * kind 5, 32 x 8, depth 1: three 256-thread CTAs per SM need <= 85
     registers a thread (65536 / 768);
   * kind 5 depth 2 and kind 6 (element copies): two CTAs per SM, <= 128;
-and none of the moment kernels may spill.  A change that breaks a budget
+  * kind 7 (TMA tensor-tile copies), 32 x 8: three CTAs per SM, <= 85;
+and none of them may spill or keep a local-memory stack frame (a run-time index
+into a constant table would put the table there).  A change that breaks a budget
 shows up here, on the CPU, before any GPU measurement.
 """
 import importlib.util
@@ -19,10 +21,12 @@ PKG = ROOT / "paper_2105_08772_gb300"
 
 ENTRY = re.compile(r"Compiling entry function '(\S+)'")
 USED = re.compile(r"Used (\d+) registers")
-SPILL = re.compile(r"(\d+) bytes spill stores, (\d+) bytes spill loads")
+SPILL = re.compile(r"(\d+) bytes stack frame, (\d+) bytes spill stores, (\d+) bytes spill loads")
 # lattice_moment_kernel<P, ST, BX, BY, D, ELEM> / lattice_moment_batch_kernel<...>, mangled
 MOMENT = re.compile(r"(lattice_moment_kernel|lattice_moment_batch_kernel)"
                     r"ILi(\d+)ELi(\d+)ELi(\d+)ELi(\d+)ELi(\d+)ELb([01])E")
+# lattice_tma_kernel<ST, BX, BY>
+TMA = re.compile(r"(lattice_tma_kernel)ILi(\d+)ELi(\d+)ELi(\d+)EE")
 
 
 def _build_module():
@@ -44,18 +48,18 @@ def moment_kernels(tmp_path_factory):
            "-o", str(obj)]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
-    out, cur, spill = {}, None, (0, 0)
+    out, cur, spill = {}, None, (0, 0, 0)
     for line in (r.stdout + r.stderr).splitlines():
         m = ENTRY.search(line)
         if m:
-            cur, spill = m.group(1), (0, 0)
+            cur, spill = m.group(1), (0, 0, 0)
             continue
         m = SPILL.search(line)
         if cur and m:
-            spill = (int(m.group(1)), int(m.group(2)))
+            spill = (int(m.group(1)), int(m.group(2)), int(m.group(3)))
         m = USED.search(line)
         if cur and m:
-            k = MOMENT.search(cur)
+            k = MOMENT.search(cur) or TMA.search(cur)
             if k:
                 key = (k.group(1),) + tuple(int(v) for v in k.groups()[1:])
                 out[key] = (int(m.group(1)), spill)
@@ -65,7 +69,7 @@ def moment_kernels(tmp_path_factory):
 
 
 def test_moment_kernels_do_not_spill(moment_kernels):
-    bad = {k: v for k, v in moment_kernels.items() if v[1] != (0, 0)}
+    bad = {k: v for k, v in moment_kernels.items() if v[1] != (0, 0, 0)}
     assert not bad, bad
 
 
@@ -75,6 +79,7 @@ def test_moment_kernels_do_not_spill(moment_kernels):
     (("lattice_moment_kernel", 1, 4, 32, 8, 2, 0), 128),       # kind 5 depth 2, 2 CTAs/SM
     (("lattice_moment_kernel", 1, 4, 32, 8, 1, 1), 128),       # kind 6, 2 CTAs/SM
     (("lattice_moment_batch_kernel", 1, 4, 32, 8, 1, 1), 128),
+    (("lattice_tma_kernel", 4, 32, 8), 85),                    # kind 7, 3 CTAs/SM
 ])
 def test_register_budget_for_the_designed_occupancy(moment_kernels, key, limit):
     assert key in moment_kernels, sorted(moment_kernels)
