@@ -44,13 +44,16 @@ struct MomentShape {
   static constexpr int VE = 16 / (int)sizeof(S);       // elements per 16-byte chunk
   static constexpr int APRON = VE > kChunkApron ? VE : kChunkApron;   // staged left of the tile
   static constexpr int XW = BX + 2 * APRON;
+  // staged row pitch: XW, or XW + 4 for FP32 32 x 8 E4 tiles, whose rows 44 floats
+  // apart put the halo ring's side columns (read by one warp) on distinct banks
+  static constexpr int XWS = (sizeof(S) == 4 && !ELEM && BX == 32 && BY == 8 && R == 1) ? XW + 4 : XW;
   static constexpr int NCH = XW / VE;
   static constexpr int NS = 1 + D;
   static constexpr int NR = 2 * R + 2;                 // psi planes (one spare: one barrier per plane)
   static constexpr int NPER = (NPAD + NT - 1) / NT;   // padded nodes a thread copies (ELEM)
   // ELEM: stage[i][j] holds population i pulled to padded node j (4- or 8-byte
   // element copies, any nx); else staged rows of XW values (16-byte chunks)
-  static constexpr size_t stage_elems = ELEM ? (size_t)Q * NPAD : (size_t)Q * PY * XW;
+  static constexpr size_t stage_elems = ELEM ? (size_t)Q * NPAD : (size_t)Q * PY * XWS;
   static constexpr size_t smem_bytes = sizeof(S) * NS * stage_elems + sizeof(T) * NR * NPAD;
   // ELEM variants run 2 CTAs per SM: the element copies go through L1, which
   // needs the capacity that more CTAs' shared memory would take
@@ -108,7 +111,7 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
   constexpr int APRON = Sh::APRON;
   constexpr int R = Sh::R, PX = Sh::PX, PY = Sh::PY, NPAD = Sh::NPAD, NT = Sh::NT, NH = Sh::NH;
   constexpr int NHPER = Sh::NHPER;
-  constexpr int XW = Sh::XW, VE = Sh::VE, NCH = Sh::NCH, NS = Sh::NS, NR = Sh::NR;
+  constexpr int XWS = Sh::XWS, VE = Sh::VE, NCH = Sh::NCH, NS = Sh::NS, NR = Sh::NR;
   S* stages = reinterpret_cast<S*>(smem_raw);
   T* ring = reinterpret_cast<T*>(stages + NS * Sh::stage_elems);
 
@@ -160,7 +163,7 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
     prow[pp][1] = y * nx;
     prow[pp][2] = wrap(y - 1, ny) * nx;
     pgx[pp] = wrap(xa + k * VE, nx);
-    psm[pp] = jy * XW + k * VE;
+    psm[pp] = jy * XWS + k * VE;
   }
   // ELEM copies (as in the pipelined kernel): padded nodes tid + s NT, their
   // wrapped source columns and row offsets for c = -1, 0, +1
@@ -191,7 +194,10 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
   for (int s = 0; s < NHPER; ++s) {
     const int hh = SPLIT ? (s == 0 ? tid - (NT - NHW) : -1) : tid + s * NT;
     const bool mine = hh >= 0 && hh < NH;
-    jh[s] = mine ? halo_node<R, PX, PY>(hh) : 0;
+    if constexpr (SPLIT && BX == 32 && BY == 8 && R == 1)   // one contiguous row per halo warp
+      jh[s] = mine ? halo_node_rows<BX, BY, R>(hh) : 0;
+    else
+      jh[s] = mine ? halo_node<R, PX, PY>(hh) : 0;
     validh[s] = mine && (jh[s] % PX) < w + 2 * R && (jh[s] / PX) < rows;
   }
   const int nplanes = zc + 2 * R;
@@ -220,12 +226,12 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
         if (grp == 0) {
 #pragma unroll
           for (int i = 0; i < ISPLIT; ++i)
-            cp_async_chunk16(st + i * PY * XW + psm[pp],
+            cp_async_chunk16(st + i * PY * XWS + psm[pp],
                              srcp[i] + (zo[cz(i) + 1] + prow[pp][cy(i) + 1] + pgx[pp]));
         } else if (NG == 2) {
 #pragma unroll
           for (int i = ISPLIT; i < Q; ++i)
-            cp_async_chunk16(st + i * PY * XW + psm[pp],
+            cp_async_chunk16(st + i * PY * XWS + psm[pp],
                              srcp[i] + (zo[cz(i) + 1] + prow[pp][cy(i) + 1] + pgx[pp]));
         }
       }
@@ -300,9 +306,9 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
 #pragma unroll
           for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(st[i * NPAD + j0], inv_scale);
         } else {
-          const S* row0 = st + (ty + R) * XW + tx + APRON;
+          const S* row0 = st + (ty + R) * XWS + tx + APRON;
 #pragma unroll
-          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XW - cx(i)], inv_scale);
+          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XWS - cx(i)], inv_scale);
         }
         T dn, jx, jy, jz;
         moments(v, dn, jx, jy, jz);
@@ -323,9 +329,9 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
           for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(st[i * NPAD + jh[s]], inv_scale);
         } else {
           const int hx = jh[s] % PX, hy = jh[s] / PX;
-          const S* row0 = st + hy * XW + hx + APRON - R;
+          const S* row0 = st + hy * XWS + hx + APRON - R;
 #pragma unroll
-          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XW - cx(i)], inv_scale);
+          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XWS - cx(i)], inv_scale);
         }
         rs[jh[s]] = psi_of<T>(n0 + sum19(v), d.eos);
       }

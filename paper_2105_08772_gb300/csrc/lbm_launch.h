@@ -97,8 +97,10 @@ constexpr int chunk_apron(size_t stored) { return 16 / (int)stored > 4 ? 16 / (i
 // dynamic shared memory of the unit-tau moment kernel: 1 + depth stages of the
 // stored type (rows of bx + 2 apron), psi ring of 2R + 2 padded planes in the
 // arithmetic type
+// (FP32 32 x 8 E4 tiles pad each staged row by 4 floats: see MomentShape::XWS)
 constexpr size_t moment_smem_bytes(size_t stored, size_t arith, int R, int bx, int by, int depth) {
-  return stored * (size_t)(1 + depth) * Q * (by + 2 * R) * (bx + 2 * chunk_apron(stored)) +
+  return stored * (size_t)(1 + depth) * Q * (by + 2 * R) *
+             (bx + 2 * chunk_apron(stored) + ((stored == 4 && bx == 32 && by == 8 && R == 1) ? 4 : 0)) +
          arith * (size_t)(2 * R + 2) * (bx + 2 * R) * (by + 2 * R);
 }
 // (bx, by, depth) compiled for the moment kernel (kind 5; tau = 1, else the

@@ -43,15 +43,16 @@ def shape(BX, BY, R, S, ELEM):
     VE = 16 // S
     APRON = max(VE, 4)
     XW = BX + 2 * APRON
+    XWS = XW + 4 if (S == 4 and not ELEM and BX == 32 and BY == 8 and R == 1) else XW   # padded pitch
     NCH = XW // VE
     POS = PY * NCH
     SPLIT = (not ELEM) and ceil32(POS) + ceil32(NH) <= NT
     NG = 1 if SPLIT else (2 if 2 * POS <= NT else 1)
     return dict(NT=NT, PX=PX, PY=PY, NPAD=NPAD, NH=NH, NHPER=(NH + NT - 1) // NT, VE=VE, APRON=APRON,
-                XW=XW, NCH=NCH, POS=POS, POSW=ceil32(POS), NHW=ceil32(NH), SPLIT=SPLIT, NG=NG,
+                XW=XW, XWS=XWS, NCH=NCH, POS=POS, POSW=ceil32(POS), NHW=ceil32(NH), SPLIT=SPLIT, NG=NG,
                 NPP=1 if NG == 2 else (POS + NT - 1) // NT, ISPLIT=10 if NG == 2 else Q,
                 NPER=(NPAD + NT - 1) // NT,
-                stage_elems=Q * NPAD if ELEM else Q * PY * XW)
+                stage_elems=Q * NPAD if ELEM else Q * PY * XWS)
 
 
 def halo_node(h, R, PX, PY):
@@ -65,6 +66,25 @@ def halo_node(h, R, PX, PY):
     return row * PX + (c if c < R else PX - 2 * R + c)
 
 
+def halo_node_rows(h, BX, BY, R):
+    """The warp-row order of the halo ring (32-wide tiles, R = 1)."""
+    PX, PY = BX + 2 * R, BY + 2 * R
+    if h < 32:
+        return h
+    h -= 32
+    if h < 32:
+        return (PY - 1) * PX + h
+    h -= 32
+    if h < PX - 32:
+        return 32 + h
+    h -= PX - 32
+    if h < PX - 32:
+        return (PY - 1) * PX + 32 + h
+    h -= PX - 32
+    row, c = 1 + h // 2, h % 2
+    return row * PX + (0 if c == 0 else PX - 1)
+
+
 def replay_plane(nx, ny, nz, BX, BY, R, S, ELEM, x0, y0, z):
     """Stage contents (global element ids) after one plane's copies, and the
     padded nodes the density pass forms with the stage index of each read."""
@@ -73,7 +93,7 @@ def replay_plane(nx, ny, nz, BX, BY, R, S, ELEM, x0, y0, z):
     w, h = min(BX, nx - x0), min(BY, ny - y0)
     rows = h + 2 * R
     xa = x0 - sh["APRON"]
-    PX, PY, XW, VE, NPAD = sh["PX"], sh["PY"], sh["XW"], sh["VE"], sh["NPAD"]
+    PX, PY, XW, VE, NPAD = sh["PX"], sh["PY"], sh["XWS"], sh["VE"], sh["NPAD"]
     zo = {c: wrap(z - c, nz) * ny * nx for c in (-1, 0, 1)}      # row of the pull in z
     stage = np.full(sh["stage_elems"], -1, dtype=np.int64)
     for tid in range(sh["NT"]):
@@ -121,7 +141,8 @@ def replay_plane(nx, ny, nz, BX, BY, R, S, ELEM, x0, y0, z):
         for s in range(sh["NHPER"]):
             hh = (tid - (sh["NT"] - sh["NHW"]) if s == 0 else -1) if sh["SPLIT"] else tid + s * sh["NT"]
             if 0 <= hh < sh["NH"]:
-                jh = halo_node(hh, R, PX, PY)
+                jh = (halo_node_rows(hh, BX, BY, R) if (sh["SPLIT"] and BX == 32 and BY == 8 and R == 1)
+                      else halo_node(hh, R, PX, PY))
                 if jh % PX < w + 2 * R and jh // PX < rows:
                     nodes.append(jh)
         for jn in nodes:
