@@ -349,6 +349,19 @@ lbm_status lbm_batch_enqueue(lbm_batch* b, lbm_box box, double tau, double G, lb
 lbm_status lbm_batch_run(lbm_batch* b, long long max_steps, long long check_every, double tol_dP_rel,
                          double tol_du, long long* lattice_updates);
 lbm_status lbm_batch_result(const lbm_batch* b, int id, lbm_obs* out);
+/* Batch autotuner: fills the slots from the queue, times `reps` (>= 2, rounded up
+ * to even) launches of the batch step for every candidate -- kernel mode (the
+ * row-chunk moment kernel, the element-copy moment kernel, the pipelined kernel,
+ * where the queue allows each), z chunk (8, 16, 32 planes) and slot count (all
+ * slots, or half of them when at least four lattices are resident) -- and keeps
+ * the one with the most lattice updates per second for lbm_batch_run.  The
+ * measured lattices are then started again from their initial drops (runs beyond
+ * the chosen slot count go back to the queue), so results do not depend on the
+ * tuning.  *choice (may be null) = mode * 10^6 + z chunk * 10^3 + slots (mode:
+ * 1 pipelined, 2 row-chunk moment, 3 element-copy moment; 0 mixed tau).
+ * Synchronises.  Errors: LBM_EINVAL for a null batch or an empty queue,
+ * LBM_ECUDA. */
+lbm_status lbm_batch_autotune(lbm_batch* b, int reps, long long* choice);
 const char* lbm_batch_last_error(const lbm_batch* b);
 void lbm_batch_destroy(lbm_batch* b);
 

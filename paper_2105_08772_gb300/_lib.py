@@ -30,7 +30,7 @@ EXPORTS = (
     "lbm_copy_velocity", "lbm_save", "lbm_load", "lbm_autotune", "lbm_set_tile", "lbm_get_tile",
     "lbm_default_tile",
     "lbm_storage_params", "lbm_density_moments_noalloc", "lbm_batch_workspace_bytes",
-    "lbm_batch_create", "lbm_batch_enqueue", "lbm_batch_run", "lbm_batch_result",
+    "lbm_batch_create", "lbm_batch_enqueue", "lbm_batch_run", "lbm_batch_result", "lbm_batch_autotune",
     "lbm_batch_last_error", "lbm_batch_destroy", "lbm_pn_profile", "lbm_flat_workspace_bytes",
     "lbm_flat_interface", "lbm_coexistence_estimate", "lbm_group_workspace_bytes", "lbm_group_create",
     "lbm_group_step", "lbm_group_last_error", "lbm_group_destroy",
@@ -108,6 +108,7 @@ def _load():
         "lbm_batch_run": (C.c_int, [_P, C.c_longlong, C.c_longlong, C.c_double, C.c_double,
                                     C.POINTER(C.c_longlong)]),
         "lbm_batch_result": (C.c_int, [_P, C.c_int, C.POINTER(lbm_obs)]),
+        "lbm_batch_autotune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong)]),
         "lbm_batch_last_error": (C.c_char_p, [_P]),
         "lbm_batch_destroy": (None, [_P]),
         "lbm_pn_profile": (C.c_int, [_P, _D, C.c_longlong]),

@@ -1292,6 +1292,12 @@ struct lbm_batch {
   int graph_len = 0;
   int graph_mode = -1;       // BatchMode the graph (and the table's tiling) was made for
   long long lattice_updates = 0;
+  // configuration chosen by lbm_batch_autotune (defaults: the natural kernel mode,
+  // z chunks of min(16, nz), every slot)
+  int mode_override = -1;
+  int zchunk = 0;
+  int slot_cap = 0;
+  std::vector<int> requeued;  // runs returned to the queue (started before next_queued)
   char err[512];
 };
 
@@ -1328,7 +1334,24 @@ BatchLayout batch_layout(int slots, lbm_box max_box, int stencil, int prec) {
 
 // kernel mode of the whole queue: the moment kernel needs tau = 1 and boxes whose
 // rows split into 16-byte chunks (nx % 4 == 0) at least a tile plus apron wide
+int natural_batch_mode(const lbm_batch* b);
+
+// the kernel modes that can run the whole queue, fastest first by construction
+std::vector<int> batch_modes_allowed(int natural) {
+  if (natural == kBatchMoment) return {kBatchMoment, kBatchMomentElem, kBatchUnitTau};
+  if (natural == kBatchMomentElem) return {kBatchMomentElem, kBatchUnitTau};
+  return {natural};
+}
+
 int batch_mode(const lbm_batch* b) {
+  const int natural = natural_batch_mode(b);
+  if (b->mode_override >= 0)
+    for (int m : batch_modes_allowed(natural))
+      if (m == b->mode_override) return m;
+  return natural;
+}
+
+int natural_batch_mode(const lbm_batch* b) {
   bool unit = true, moment = true;
   const int bx = batch_tile(b->prec, b->stencil, kBatchMoment).bx;
   for (const BatchRun& r : b->runs) {
@@ -1339,9 +1362,16 @@ int batch_mode(const lbm_batch* b) {
 }
 
 lbm_status batch_fill(lbm_batch* b) {
-  for (int k = 0; k < b->slots; ++k) {
-    while (!b->slot_ctx[k] && b->next_queued < b->runs.size()) {
-      const int id = (int)b->next_queued++;
+  const int cap = b->slot_cap > 0 && b->slot_cap < b->slots ? b->slot_cap : b->slots;
+  for (int k = 0; k < cap; ++k) {
+    while (!b->slot_ctx[k] && (!b->requeued.empty() || b->next_queued < b->runs.size())) {
+      int id;
+      if (!b->requeued.empty()) {
+        id = b->requeued.back();
+        b->requeued.pop_back();
+      } else {
+        id = (int)b->next_queued++;
+      }
       BatchRun& r = b->runs[id];
       lbm_ctx* c = nullptr;
       lbm_status st = lbm_create(r.box, r.tau, r.G, r.eos, b->stencil, b->prec, b->ws + k * b->slot_bytes,
@@ -1379,7 +1409,8 @@ lbm_status batch_upload(lbm_batch* b) {
     BatchEntry e;
     e.d = desc_of(c, 0);
     e.parity = c->cur;
-    e.zchunk = c->box.nz < 16 ? c->box.nz : 16;
+    const int zc = b->zchunk > 0 ? b->zchunk : 16;
+    e.zchunk = c->box.nz < zc ? c->box.nz : zc;
     e.item_begin = items;
     items += (long long)((c->box.nx + t.bx - 1) / t.bx) * ((c->box.ny + t.by - 1) / t.by) *
              ((c->box.nz + e.zchunk - 1) / e.zchunk);
@@ -1563,6 +1594,104 @@ lbm_status lbm_batch_run(lbm_batch* b, long long max_steps, long long check_ever
     if (st != LBM_OK) return st;
   }
   if (lattice_updates) *lattice_updates = b->lattice_updates;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int reps, long long* choice) {
+  NvtxRange nvtx("lbm_batch_autotune");
+  if (!b) return bfail(nullptr, LBM_EINVAL, "null batch");
+  if (reps < 2) reps = 2;
+  reps += reps & 1;
+  lbm_status st = batch_fill(b);
+  if (st != LBM_OK) return st;
+  std::vector<int> filled;
+  for (int k = 0; k < b->slots; ++k)
+    if (b->slot_ctx[k]) filled.push_back(k);
+  if (filled.empty()) return bfail(b, LBM_EINVAL, "autotune needs queued runs");
+  const int natural = natural_batch_mode(b);
+  std::vector<int> caps = {b->slots};
+  if ((int)filled.size() >= 4) caps.push_back((b->slots + 1) / 2);
+  cudaEvent_t e0, e1;
+  LBM_BCUDA(b, cudaEventCreate(&e0));
+  LBM_BCUDA(b, cudaEventCreate(&e1));
+  int best_mode = natural, best_zc = 0, best_cap = b->slots;
+  double best_rate = -1.0;
+  const int save_cap = b->slot_cap;
+  for (int mode : batch_modes_allowed(natural)) {
+    for (int zc : {8, 16, 32}) {
+      for (int cap : caps) {
+        b->mode_override = mode;
+        b->zchunk = zc;
+        b->slot_cap = cap;   // the first `cap` slots take part in the measurement
+        long long nodes = 0;
+        for (int k = 0; k < b->slots && k < cap; ++k)
+          if (b->slot_ctx[k]) nodes += (long long)b->slot_ctx[k]->box.nx * b->slot_ctx[k]->box.ny * b->slot_ctx[k]->box.nz;
+        if (!nodes) continue;
+        // time `reps` launches over the table restricted to the first cap slots
+        std::vector<lbm_ctx*> hidden(b->slots, nullptr);
+        for (int k = cap; k < b->slots; ++k) std::swap(hidden[k], b->slot_ctx[k]);
+        b->graph_mode = mode;   // the table's tiling follows the kernel launched
+        st = batch_upload(b);
+        int grid = 0;
+        cudaError_t ce = cudaSuccess;
+        if (st == LBM_OK)
+          ce = launch_batch(b->prec, b->stencil, mode, b->table_dev, b->hdr_dev, 0, true, &grid, b->stream);
+        for (int r = 0; r < 2 && st == LBM_OK && ce == cudaSuccess; ++r)
+          ce = launch_batch(b->prec, b->stencil, mode, b->table_dev, b->hdr_dev, r & 1, false, nullptr, b->stream);
+        if (st == LBM_OK && ce == cudaSuccess) ce = cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < reps && st == LBM_OK && ce == cudaSuccess; ++r)
+          ce = launch_batch(b->prec, b->stencil, mode, b->table_dev, b->hdr_dev, r & 1, false, nullptr, b->stream);
+        if (st == LBM_OK && ce == cudaSuccess) ce = cudaEventRecord(e1, b->stream);
+        if (st == LBM_OK && ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        for (int k = cap; k < b->slots; ++k) std::swap(hidden[k], b->slot_ctx[k]);
+        if (st != LBM_OK || ce != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          b->slot_cap = save_cap;
+          b->mode_override = -1;
+          b->zchunk = 0;
+          return st != LBM_OK ? st : bfail(b, LBM_ECUDA, "batch autotune: %s", cudaGetErrorString(ce));
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double rate = (double)nodes * reps / (ms * 1e-3);
+        if (rate > best_rate) {
+          best_rate = rate;
+          best_mode = mode;
+          best_zc = zc;
+          best_cap = cap;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->mode_override = best_mode;
+  b->zchunk = best_zc;
+  b->slot_cap = best_cap;
+  // the timed launches advanced the resident lattices: start them again from their
+  // initial drops; those beyond the chosen slot count go back to the queue
+  for (int k = 0; k < b->slots; ++k) {
+    lbm_ctx* c = b->slot_ctx[k];
+    if (!c) continue;
+    const int id = b->slot_run[k];
+    BatchRun& r = b->runs[id];
+    if (k >= best_cap) {
+      lbm_destroy(c);
+      b->slot_ctx[k] = nullptr;
+      b->slot_run[k] = -1;
+      r.state = 0;
+      b->requeued.push_back(id);
+      continue;
+    }
+    st = lbm_init_drop(c, r.center, r.R, r.rho_in, r.rho_out, r.width);
+    if (st == LBM_OK) st = lbm_observables(c, &r.obs);
+    if (st != LBM_OK) return bfail(b, st, "run %d: %s", id, c->err);
+  }
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_mode = -1;
+  if (choice) *choice = (long long)best_mode * 1000000 + (long long)best_zc * 1000 + best_cap;
   return LBM_OK;
 }
 

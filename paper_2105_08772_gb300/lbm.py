@@ -269,6 +269,15 @@ def lbm_batch_run(b, max_steps=50_000, check_every=2048, tol_dP_rel=1e-5, tol_du
     return lu.value
 
 
+def lbm_batch_autotune(b, reps: int = 8) -> int:
+    """Time the batch step's kernel modes, z chunks and slot counts on the resident
+    lattices and keep the fastest; returns the choice code (mode 10^6 + z chunk 10^3 +
+    slots)."""
+    code = C.c_longlong()
+    _bcheck(_lib_.lbm_batch_autotune(b, int(reps), C.byref(code)), b)
+    return code.value
+
+
 def lbm_batch_result(b, rid: int):
     """(status, lbm_obs) of a finished run; the status is returned, not raised."""
     o = lbm_obs()
@@ -308,6 +317,9 @@ class Batch:
 
     def run(self, **kw) -> int:
         return lbm_batch_run(self.b, **kw)
+
+    def autotune(self, reps: int = 8) -> int:
+        return lbm_batch_autotune(self.b, reps)
 
     def result(self, rid: int):
         return lbm_batch_result(self.b, rid)

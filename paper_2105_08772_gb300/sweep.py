@@ -164,8 +164,9 @@ def _sync():
 
 def run_batched(runs, coex, slots: int = 64, prec: str = "f32", stencil: str = "E4",
                 max_steps: int = 50_000, check_every: int = 2048, tol_dP_rel: float = 1e-5,
-                tol_du: float = 1e-12, width: float = 1.0):
-    """All runs through one lbm_batch.  Returns (outcomes, wall seconds, lattice updates)."""
+                tol_du: float = 1e-12, width: float = 1.0, autotune: bool = False):
+    """All runs through one lbm_batch (after lbm_batch_autotune if asked).  Returns
+    (outcomes, wall seconds, lattice updates); the tuning time is in the wall time."""
     L = max(r.L for r in runs)
     _sync()
     t0 = time.perf_counter()
@@ -176,6 +177,8 @@ def run_batched(runs, coex, slots: int = 64, prec: str = "f32", stencil: str = "
             n_in, n_out = _densities(r, coex)
             ids.append(b.enqueue((r.L, r.L, r.L), tau=r.tau, G=r.G, psi=r.psi, R=r.R, rho_in=n_in,
                                  rho_out=n_out, width=width))
+        if autotune:
+            b.autotune()
         lu = b.run(max_steps=max_steps, check_every=check_every, tol_dP_rel=tol_dP_rel, tol_du=tol_du)
         outs = []
         for r, rid in zip(runs, ids):
@@ -338,6 +341,7 @@ def main(argv=None) -> dict:
     ap.add_argument("--per-R", type=float, default=4.0)
     ap.add_argument("--plain", default="", help="couplings also run one lattice at a time in FP64")
     ap.add_argument("--out", default="")
+    ap.add_argument("--autotune", action="store_true", help="lbm_batch_autotune before each batch run")
     ap.add_argument("--paper", action="store_true",
                     help="the paper's sweep: 12 reduced couplings x 2 psi x odd L (see --max-L)")
     ap.add_argument("--max-L", type=int, default=335, help="largest box side of --paper")
@@ -366,7 +370,8 @@ def main(argv=None) -> dict:
         coex = coexistence(couplings, psi=a.psi)
     t_flat = time.perf_counter() - t0
     mine = shard(runs, rank, world)
-    outs, wall, lu = run_batched(mine, coex, slots=a.slots, prec=a.prec, max_steps=a.max_steps)
+    outs, wall, lu = run_batched(mine, coex, slots=a.slots, prec=a.prec, max_steps=a.max_steps,
+                                 autotune=a.autotune)
     if world > 1:
         outs = gather_outcomes(outs)
         wall = max_over_ranks(wall)
@@ -411,7 +416,8 @@ def main(argv=None) -> dict:
         outs_p, wall_p, lu_p = run_plain(sub, coex, prec="f64", max_steps=a.max_steps)
         fit_p = tolman(outs_p, coex)
         # the batched path on the same subset alone, for a like-for-like wall time
-        outs_s, wall_s, lu_s = run_batched(sub, coex, slots=a.slots, prec=a.prec, max_steps=a.max_steps)
+        outs_s, wall_s, lu_s = run_batched(sub, coex, slots=a.slots, prec=a.prec, max_steps=a.max_steps,
+                                           autotune=a.autotune)
         report["plain_f64"] = {"runs": len(sub), "wall_s": wall_p, "lattice_updates": lu_p,
                                "MLUPS": lu_p / wall_p / 1e6,
                                "fit": {str(G): asdict(r) for G, r in fit_p.items()}}

@@ -100,6 +100,7 @@ def test_create_rejects_bad_arguments_before_any_gpu_work(kw, status, msg):
 
 def test_null_context_calls_fail_cleanly():
     assert _lib.lib.lbm_step(None, 1) == _lib.LBM_EINVAL
+    assert _lib.lib.lbm_batch_autotune(None, 4, None) == _lib.LBM_EINVAL
     assert _lib.lib.lbm_observables(None, None) == _lib.LBM_EINVAL
     _lib.lib.lbm_destroy(None)
     assert _lib.lib.lbm_strerror(_lib.LBM_ENOTCONV) == b"not converged"

@@ -119,3 +119,30 @@ def test_batch_rejects_boxes_larger_than_its_slots():
     b = P.Batch(1, (16, 16, 16), prec="f32")
     with pytest.raises(P.LBMError):
         b.enqueue((17, 16, 16))
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_autotuned_batch_equals_single_lattice_runs(prec):
+    """lbm_batch_autotune times kernel modes, z chunks and slot counts on the resident
+    lattices, then starts them again from their drops: the tuned batch still gives each
+    lattice bitwise what it gives alone (every kernel kind and z chunk computes the same
+    values)."""
+    steps, check = 256, 128
+    runs = RUNS_UNIT_TAU + [((40, 40, 40), 1.0, -5.0, 9.0, 1.89, 0.12)]
+    b = P.Batch(4, (48, 40, 40), prec=prec)
+    ids = [b.enqueue(box, tau=tau, G=G, R=R, rho_in=ri, rho_out=ro) for box, tau, G, R, ri, ro in runs]
+    code = b.autotune(reps=4)
+    mode, zc, slots = code // 1000000, code // 1000 % 1000, code % 1000
+    assert mode in (1, 2, 3) and zc in (8, 16, 32) and slots in (2, 4), code
+    b.run(max_steps=steps, check_every=check, tol_dP_rel=-1.0, tol_du=-1.0)
+    for rid, (box, tau, G, R, ri, ro) in zip(ids, runs):
+        st, ob = b.result(rid)
+        assert st == P._lib.LBM_ENOTCONV and ob.steps == steps, (rid, st, ob.steps)
+        lat = P.Lattice(*box, tau=tau, G=G, prec=prec)
+        lat.init_drop((box[0] // 2, box[1] // 2, box[2] // 2), R, ri, ro)
+        lat.step(steps)
+        ref = lat.observables()
+        for k in STATE_KEYS:
+            a, r = getattr(ob, k), getattr(ref, k)
+            assert (a == r) or (np.isnan(a) and np.isnan(r)), (rid, k, a, r)
+        lat.close()
