@@ -63,15 +63,12 @@ KERNEL_SOURCES = ("lbm_common.cuh", "lbm_kernels.cuh", "lbm_kernels_async.cuh", 
 PROFILE_STEMS = {7: "lattice_tma", 6: "lattice_moment_elem", 5: "lattice_moment"}
 
 
-def measured_traffic(prec, kind=5):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary of the
-    128^3 workload, or None when there is none for this kernel and precision or the
-    kernel sources changed since."""
+def profile_fields(stem, prec, box=128):
+    """The machine-readable lines (``key: value``) of a committed ncu summary, or None
+    when there is none or the kernel sources changed since it was captured (its
+    source_sha256 differs from the current sources')."""
     import hashlib
-    stem = PROFILE_STEMS.get(int(kind))
-    if stem is None:
-        return None
-    summary = ROOT / "profiles" / f"{stem}_{prec}_128.md"
+    summary = ROOT / "profiles" / f"{stem}_{prec}_{box}.md"
     if not summary.exists():
         return None
     fields = {}
@@ -81,9 +78,36 @@ def measured_traffic(prec, kind=5):
             fields[k.strip()] = v.strip()
     csrc = ROOT / "paper_2105_08772_gb300" / "csrc"
     h = hashlib.sha256(b"".join((csrc / f).read_bytes() for f in KERNEL_SOURCES)).hexdigest()
-    if fields.get("source_sha256") != h or "traffic_bytes_per_launch" not in fields:
+    if fields.get("source_sha256") != h:
+        return None
+    fields["path"] = str(summary.relative_to(ROOT))
+    return fields
+
+
+def measured_traffic(prec, kind=5):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary of the
+    128^3 workload, or None when there is none for this kernel and precision or the
+    kernel sources changed since."""
+    stem = PROFILE_STEMS.get(int(kind))
+    fields = profile_fields(stem, prec) if stem else None
+    if not fields or "traffic_bytes_per_launch" not in fields:
         return None
     return int(fields["traffic_bytes_per_launch"])
+
+
+def fp64_bound(hbm_gbs, peak):
+    """What bounds the FP64 step: this run's DRAM fraction, and the FP64 pipe's load
+    from the committed ncu summary when it was taken on the current sources (else
+    the bound is left null)."""
+    frac = hbm_gbs / peak
+    prof = profile_fields("lattice_moment", "f64")
+    pipe = float(prof["fp64_pipe_pct"]) if prof and "fp64_pipe_pct" in prof else None
+    bound = None
+    evidence = f"this run: DRAM at {100 * frac:.1f}% of the measured HBM peak"
+    if pipe is not None:
+        bound = "alu" if pipe >= 50.0 and frac < 0.5 else ("hbm" if frac >= 0.5 else None)
+        evidence += f"; ncu on the current sources: FP64 pipe {pipe:.1f}% busy ({prof['path']})"
+    return {"hbm_frac": frac, "bound": bound, "evidence": evidence}
 
 
 KERNEL_KINDS = {
@@ -486,9 +510,7 @@ def main():
         fp64 = {"value": N * LBM_STEPS_PER_STEP / (ms * 1e-3) / 1e6, "unit": "MLUPS",
                 "sample": "one 2048-step interval of the 128^3 droplet, FP64 storage and arithmetic",
                 "hbm_gbs": BYTES_PER_LU["f64"] * N * LBM_STEPS_PER_STEP / (ms * 1e-3) / 1e9,
-                "bound": "alu",
-                "evidence": "ncu: FP64 pipe 81% busy, DRAM throughput 6.6% of peak "
-                            "(profiles/lattice_moment_f64_128.md)"}
+                **fp64_bound(BYTES_PER_LU["f64"] * N * LBM_STEPS_PER_STEP / (ms * 1e-3) / 1e9, peak)}
 
     # the same step kernel on a 256^3 lattice (4x the 128^3 working set): the
     # roofline fraction at a size well past L2

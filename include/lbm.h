@@ -365,6 +365,60 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int reps, long long* choice);
 const char* lbm_batch_last_error(const lbm_batch* b);
 void lbm_batch_destroy(lbm_batch* b);
 
+/* ---------------------------------------------------------------- z-slab decomposition */
+
+/* One lattice split along z over `world` slabs (one process and GPU each), for
+ * boxes larger than one GPU holds.  The update of Eq. (3) is local (Sec. II,
+ * below Eq. (3)): the new populations of a node depend on the stored
+ * populations within R + 1 planes, R the force stencil's radius (1 for E4, 2 for
+ * E6 / E8).  Each slab is its own context of nx x ny x (owned + 2(R + 1)) nodes:
+ * local planes 0..R are the ghost planes below the owned ones, then the owned
+ * planes, then R + 1 ghost planes above.  It is stepped as a periodic lattice
+ * (lbm_step); the wrap-around then reaches only ghost planes, whose results are
+ * discarded, so the owned planes evolve exactly as in the whole lattice.  After
+ * every step the ghost planes' needed populations are copied from the
+ * neighbouring slabs (slab r - 1 below, r + 1 above, periodic in r).
+ *
+ * lbm_slab_partition: contiguous, balanced slabs of nz planes; z_begin (host
+ * array of world + 1 ints) receives slab r's first global plane in z_begin[r]
+ * and nz in z_begin[world].  LBM_EINVAL for a null pointer, nz or world < 1, or
+ * a slab thinner than R + 1 planes (its ghost planes would reach past its
+ * neighbours). */
+lbm_status lbm_slab_partition(int nz, int world, int stencil, int* z_begin);
+
+/* The populations (bit i = population i, order above) that ghost plane k
+ * (1..R + 1, counted outward from the owned planes) on side -1 (below) or +1
+ * (above) must hold before a step: those with c_z pointing into the slab for
+ * k <= R + 1, c_z = 0 for k <= R, c_z pointing away for k <= R - 1 -- 19 R
+ * population planes per side, against 19 (R + 1) for whole ghost planes.
+ * LBM_EINVAL for a null mask, an unknown stencil, side not +-1 or k out of range. */
+lbm_status lbm_slab_halo_mask(int stencil, int side, int k, unsigned* mask);
+
+/* lbm_set_populations with the storage shift and scale given instead of derived
+ * from the field, so that every slab of one lattice stores alike (take them
+ * from lbm_storage_params of a context holding the whole field, or agree on
+ * them across processes).  n0 is ignored for FP64 storage; scale must be 1 for
+ * FP64 / FP32 and a power of two for FP16.  LBM_EINVAL otherwise, or as
+ * lbm_set_populations. */
+lbm_status lbm_set_populations_storage(lbm_ctx* ctx, const double* host_f, double n0, double scale);
+
+/* Device address and size in bytes of population i's plane z of the current
+ * state (stored type: 8, 4 or 2 bytes per node; FP32 / FP16 hold
+ * (f_i - w_i n0) * scale).  The address is valid until the next step, which
+ * swaps the state buffers.  For exchanges between processes (e.g.
+ * torch.distributed send / recv of these planes).  LBM_EINVAL for null pointers
+ * or an index out of range. */
+lbm_status lbm_state_plane(const lbm_ctx* ctx, int i, int z, void** dev_ptr, size_t* bytes);
+
+/* Copy the populations in mask (bit i = population i) of plane src_z of src's
+ * current state into plane dst_z of dst's current state (slabs in one process,
+ * on the same or peer devices).  Enqueued on dst's stream after the work already
+ * queued on src's stream; the caller keeps src from stepping twice more before
+ * the copy has run (one stream for all slabs does).  Both contexts must have
+ * the same nx, ny, storage precision and storage parameters (LBM_EINVAL
+ * otherwise, or for a plane out of range or mask bits above 18). */
+lbm_status lbm_halo_copy(lbm_ctx* dst, int dst_z, const lbm_ctx* src, int src_z, unsigned mask);
+
 /* ---------------------------------------------------------------- no-allocation variant */
 
 /* Mass and centre of mass of a density field, for callers that cannot allocate

@@ -35,6 +35,8 @@ EXPORTS = (
     "lbm_flat_interface", "lbm_coexistence_estimate", "lbm_group_workspace_bytes", "lbm_group_create",
     "lbm_group_step", "lbm_group_last_error", "lbm_group_destroy",
     "lbm_strerror", "lbm_last_error", "lbm_tolman_fit",
+    "lbm_slab_partition", "lbm_slab_halo_mask", "lbm_set_populations_storage", "lbm_state_plane",
+    "lbm_halo_copy",
 )
 
 
@@ -119,6 +121,11 @@ def _load():
         "lbm_group_step": (C.c_int, [_P, C.c_longlong]),
         "lbm_group_last_error": (C.c_char_p, [_P]),
         "lbm_group_destroy": (None, [_P]),
+        "lbm_slab_partition": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+        "lbm_slab_halo_mask": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_uint)]),
+        "lbm_set_populations_storage": (C.c_int, [_P, _D, C.c_double, C.c_double]),
+        "lbm_state_plane": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(_P), C.POINTER(C.c_size_t)]),
+        "lbm_halo_copy": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_uint]),
         "lbm_flat_interface": (C.c_int, [C.c_double, C.c_double, lbm_eos, C.c_int, C.c_int, C.c_int,
                                          C.c_double, C.c_double, C.c_longlong, C.c_double, _P,
                                          C.c_size_t, _P, _D, _D, _D, C.POINTER(C.c_longlong)]),

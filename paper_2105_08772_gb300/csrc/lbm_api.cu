@@ -1243,6 +1243,112 @@ lbm_status lbm_tolman_fit(const double* R_s, const double* sigma_s, const int* i
   return LBM_OK;
 }
 
+// ---------------------------------------------------------------- z-slab decomposition
+// One lattice split along z over several processes.  The update of Eq. (3) is
+// local (Sec. II, below Eq. (3)): a node's new populations depend on the stored
+// populations of the nodes within R + 1 planes (pull, then the density of the
+// psi neighbours within R).  Each slab is stepped as a periodic lattice of its
+// owned planes plus R + 1 ghost planes on each side; wrap-around then reaches
+// only ghost planes, and after every step the ghost planes' needed populations
+// are copied from the neighbouring slabs.
+
+lbm_status lbm_slab_partition(int nz, int world, int stencil, int* z_begin) {
+  if (!z_begin) return fail(nullptr, LBM_EINVAL, "z_begin is null");
+  if (!valid_stencil(stencil)) return fail(nullptr, LBM_EINVAL, "stencil must be 4, 6 or 8");
+  if (world < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "nz and world must be >= 1");
+  const int H = radius_of(stencil) + 1;
+  if (nz / world < H)
+    return fail(nullptr, LBM_EINVAL, "%d planes over %d slabs leave fewer than %d planes in a slab", nz, world, H);
+  const int base = nz / world, extra = nz % world;
+  z_begin[0] = 0;
+  for (int r = 0; r < world; ++r) z_begin[r + 1] = z_begin[r] + base + (r < extra ? 1 : 0);
+  return LBM_OK;
+}
+
+lbm_status lbm_slab_halo_mask(int stencil, int side, int k, unsigned* mask) {
+  if (!mask) return fail(nullptr, LBM_EINVAL, "mask is null");
+  if (!valid_stencil(stencil)) return fail(nullptr, LBM_EINVAL, "stencil must be 4, 6 or 8");
+  const int R = radius_of(stencil);
+  if ((side != -1 && side != 1) || k < 1 || k > R + 1)
+    return fail(nullptr, LBM_EINVAL, "side must be -1 or +1 and k in 1..%d", R + 1);
+  // Stored slot i of node y streams to y + xi_i.  Ghost plane k below the slab
+  // (z0 - k) feeds the pull of owned plane z0 (k = 1, c_z = +1) and the density
+  // of ghost planes z0 - j, j = 1..R, which pulls slot i from plane z0 - j - c_z:
+  // c_z = +1 is needed for k <= R + 1, c_z = 0 for k <= R, c_z = -1 for
+  // k <= R - 1.  Above the slab the signs of c_z swap.
+  unsigned m = 0;
+  for (int i = 0; i < Q; ++i) {
+    const int c = side * cz(i);   // +1: towards the slab
+    const bool need = c == -1 ? k <= R + 1 : (c == 0 ? k <= R : k <= R - 1);
+    if (need) m |= 1u << i;
+  }
+  *mask = m;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_populations_storage(lbm_ctx* c, const double* host_f, double n0, double scale) {
+  LBM_CHECK_CTX(c);
+  if (!(isfinite(n0) && isfinite(scale) && scale > 0))
+    return fail(c, LBM_EINVAL, "n0 must be finite and scale positive");
+  if (c->prec != kF16 && scale != 1.0) return fail(c, LBM_EINVAL, "scale must be 1 for FP64 and FP32 storage");
+  int ex = 0;
+  if (c->prec == kF16 && frexp(scale, &ex) != 0.5) return fail(c, LBM_EINVAL, "scale must be a power of two");
+  lbm_status st = lbm_set_populations(c, host_f);
+  if (st != LBM_OK || c->prec == kF64) return st;
+  // rewrite the field under the given storage parameters
+  c->n0 = n0;
+  c->scale = scale;
+  const long long N = (long long)c->box.nx * c->box.ny * c->box.nz;
+  double* tmp = static_cast<double*>(c->pop[1]);
+  LatticeDesc d = desc_of(c, 1);   // writes pop[0]
+  for (int i = 0; i < Q; ++i) {
+    LBM_CUDA(c, cudaMemcpyAsync(tmp, host_f + (long long)i * N, N * sizeof(double),
+                                cudaMemcpyHostToDevice, c->stream));
+    LBM_CUDA(c, launch_set_plane(c->prec, d, i, tmp, c->stream));
+  }
+  return reset_history(c);
+}
+
+lbm_status lbm_state_plane(const lbm_ctx* c, int i, int z, void** dev_ptr, size_t* bytes) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "null context");
+  if (!dev_ptr || !bytes) return fail(nullptr, LBM_EINVAL, "dev_ptr or bytes is null");
+  if (i < 0 || i >= Q || z < 0 || z >= c->box.nz) return fail(nullptr, LBM_EINVAL, "population or plane out of range");
+  const size_t es = c->prec == kF64 ? 8 : (c->prec == kF32 ? 4 : 2);
+  const size_t plane = (size_t)c->box.nx * c->box.ny;
+  *bytes = plane * es;
+  *dev_ptr = static_cast<char*>(c->pop[c->cur]) + ((size_t)i * c->box.nz + z) * plane * es;
+  return LBM_OK;
+}
+
+lbm_status lbm_halo_copy(lbm_ctx* dst, int dst_z, const lbm_ctx* src, int src_z, unsigned mask) {
+  LBM_CHECK_CTX(dst);
+  if (!src) return fail(dst, LBM_EINVAL, "src is null");
+  if (src->box.nx != dst->box.nx || src->box.ny != dst->box.ny || src->prec != dst->prec ||
+      src->n0 != dst->n0 || src->scale != dst->scale)
+    return fail(dst, LBM_EINVAL, "slabs differ in plane size, storage precision or storage parameters");
+  if (mask >> Q) return fail(dst, LBM_EINVAL, "mask has bits above population %d", Q - 1);
+  if (dst_z < 0 || dst_z >= dst->box.nz || src_z < 0 || src_z >= src->box.nz)
+    return fail(dst, LBM_EINVAL, "plane out of range");
+  if (src != dst && src->stream != dst->stream) {
+    // the copy follows the source's queued steps
+    cudaEvent_t ev;
+    LBM_CUDA(dst, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, src->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(dst->stream, ev, 0);
+    cudaEventDestroy(ev);
+    LBM_CUDA(dst, e);
+  }
+  for (int i = 0; i < Q; ++i) {
+    if (!((mask >> i) & 1u)) continue;
+    void *s = nullptr, *d = nullptr;
+    size_t b = 0;
+    lbm_state_plane(src, i, src_z, &s, &b);
+    lbm_state_plane(dst, i, dst_z, &d, &b);
+    LBM_CUDA(dst, cudaMemcpyAsync(d, s, b, cudaMemcpyDefault, dst->stream));
+  }
+  return LBM_OK;
+}
+
 }  // extern "C"
 
 // ====================================================================== batches

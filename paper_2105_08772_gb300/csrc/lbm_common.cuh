@@ -137,4 +137,16 @@ __host__ __device__ __forceinline__ int wrap(int g, int n) {
   return g < 0 ? g + n : (g >= n ? g - n : g);
 }
 
+// Programmatic dependent launch (sm_90 and later).  The step kernels are
+// launched with programmatic stream serialisation, so the next step's CTAs are
+// scheduled into the slots this step's CTAs free instead of after the whole
+// grid has drained.  Each CTA first allows its own successor to be scheduled,
+// then waits until the previous grid has completed and its writes are visible;
+// no global memory is touched before that wait.  Without the launch attribute
+// both instructions are no-ops.
+__device__ __forceinline__ void step_grid_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 }  // namespace lbm

@@ -210,6 +210,7 @@ template <int P, int ST, int BX, int BY, int D, bool UNIT_TAU>
 __global__ void __launch_bounds__(BX * BY, (async_min_blocks<BX * BY, AsyncShape<P, ST, BX, BY, D>::smem_bytes>()))
 lattice_async_kernel(LatticeDesc d, int zchunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  step_grid_enter();
   const int ncols = ((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
   const long long items = (long long)ncols * ((d.nz + zchunk - 1) / zchunk);
 #pragma unroll 1
@@ -239,6 +240,7 @@ __global__ void __launch_bounds__(BX * BY)
 lattice_async_batch_kernel(const BatchEntry* __restrict__ table, const BatchHeader* __restrict__ hdr,
                            int step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  step_grid_enter();
   const int n = hdr->n;
   const long long total = hdr->total_items;
 #pragma unroll 1

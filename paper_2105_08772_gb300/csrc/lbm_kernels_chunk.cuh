@@ -195,6 +195,7 @@ template <int P, int ST, int BX, int BY, int D, bool UNIT_TAU>
 __global__ void __launch_bounds__(BX * BY, (async_min_blocks<BX * BY, ChunkShape<P, ST, BX, BY, D>::smem_bytes>()))
 lattice_chunk_kernel(LatticeDesc d, int zchunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  step_grid_enter();
   const int ncols = ((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
   const long long items = (long long)ncols * ((d.nz + zchunk - 1) / zchunk);
 #pragma unroll 1

@@ -344,6 +344,7 @@ template <int P, int ST, int BX, int BY, int D, bool ELEM = false>
 __global__ void __launch_bounds__(BX * BY, (MomentShape<P, ST, BX, BY, D, ELEM>::MIN_BLOCKS))
 lattice_moment_kernel(LatticeDesc d, int zchunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  step_grid_enter();
   const int ncols = ((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY);
   const long long items = (long long)ncols * ((d.nz + zchunk - 1) / zchunk);
 #pragma unroll 1
@@ -358,6 +359,7 @@ __global__ void __launch_bounds__(BX * BY, (MomentShape<P, ST, BX, BY, D, ELEM>:
 lattice_moment_batch_kernel(const BatchEntry* __restrict__ table, const BatchHeader* __restrict__ hdr,
                             int step) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  step_grid_enter();
   const int n = hdr->n;
   const long long total = hdr->total_items;
 #pragma unroll 1

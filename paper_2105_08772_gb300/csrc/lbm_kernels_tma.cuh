@@ -536,6 +536,7 @@ lattice_tma_kernel(LatticeDesc d, const __grid_constant__ TmaMapSet maps, int zc
   }
   if (threadIdx.x < Sh::NMAPS)
     asm volatile("prefetch.tensormap [%0];\n" ::"l"((unsigned long long)&maps.map[threadIdx.x]) : "memory");
+  step_grid_enter();
   __syncthreads();
   unsigned phase_bits = 0;
   const int ncols = ((d.nx + BX - 1) / BX) * (d.ny / BY);

@@ -43,6 +43,26 @@ inline int choose_zchunk(long long cols, int nz, int R, long long resident, int 
   return best_zc;
 }
 
+// Step kernels are launched with programmatic stream serialisation (each
+// begins with step_grid_enter): the next step's CTAs take the slots this
+// step's CTAs free and wait on the device for its completion, so consecutive
+// steps' launch latency and CTA ramp overlap the previous step's tail.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_step_kernel(void (*kern)(KArgs...), long long grid, int threads, size_t smem,
+                                      cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <typename Kern>
 static cudaError_t prepare_persistent(Kern kern, int threads, size_t smem, int* resident) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -76,8 +96,7 @@ static cudaError_t launch_async_variant(const LatticeDesc& d, int zchunk, bool p
   const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
   const long long items = cols * ((d.nz + zc - 1) / zc);
   const long long grid = items < resident ? items : resident;
-  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, zc);
-  return cudaGetLastError();
+  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, d, zc);
 }
 
 template <int P, int ST, int BX, int BY, int D, bool UNIT_TAU>
@@ -97,8 +116,7 @@ static cudaError_t launch_chunk_variant(const LatticeDesc& d, int zchunk, bool p
   const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
   const long long items = cols * ((d.nz + zc - 1) / zc);
   const long long grid = items < resident ? items : resident;
-  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, zc);
-  return cudaGetLastError();
+  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, d, zc);
 }
 
 template <int P, int ST, int BX, int BY, int D>
@@ -136,8 +154,7 @@ static cudaError_t launch_moment(const LatticeDesc& d, int zchunk, bool prepare,
   const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
   const long long items = cols * ((d.nz + zc - 1) / zc);
   const long long grid = items < resident ? items : resident;
-  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, zc);
-  return cudaGetLastError();
+  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, d, zc);
 }
 
 template <int P, int ST>
@@ -226,8 +243,7 @@ static cudaError_t launch_moment_elem(const LatticeDesc& d, int zchunk, bool pre
   const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
   const long long items = cols * ((d.nz + zc - 1) / zc);
   const long long grid = items < resident ? items : resident;
-  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, zc);
-  return cudaGetLastError();
+  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, d, zc);
 }
 
 template <int P, int ST>
@@ -282,8 +298,7 @@ static cudaError_t launch_batch_variant(const BatchEntry* table, const BatchHead
   }
   if (grid) *grid = resident;
   if (prepare) return cudaSuccess;
-  kern<<<(unsigned)resident, Sh::NT, Sh::smem_bytes, s>>>(table, hdr, step);
-  return cudaGetLastError();
+  return launch_step_kernel(kern, resident, Sh::NT, Sh::smem_bytes, s, table, hdr, step);
 }
 
 template <int P, int ST, int BX, int BY, int D, bool ELEM = false>
@@ -308,8 +323,7 @@ static cudaError_t launch_moment_batch_variant(const BatchEntry* table, const Ba
   }
   if (grid) *grid = resident;
   if (prepare) return cudaSuccess;
-  kern<<<(unsigned)resident, Sh::NT, Sh::smem_bytes, s>>>(table, hdr, step);
-  return cudaGetLastError();
+  return launch_step_kernel(kern, resident, Sh::NT, Sh::smem_bytes, s, table, hdr, step);
 }
 
 // batches: the moment kernel when every lattice allows it, else the pipelined
@@ -370,8 +384,7 @@ static cudaError_t launch_tma(const LatticeDesc& d, int zchunk, bool prepare, cu
   const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
   const long long items = cols * ((d.nz + zc - 1) / zc);
   const long long grid = items < resident ? items : resident;
-  kern<<<(unsigned)grid, Sh::NT, Sh::smem_bytes, s>>>(d, maps, zc);
-  return cudaGetLastError();
+  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, d, maps, zc);
 }
 
 template <int P, int ST>

@@ -166,6 +166,37 @@ def lbm_storage_params(ctx) -> tuple[float, float]:
     return n0.value, sc.value
 
 
+def lbm_slab_partition(nz: int, world: int, stencil: int) -> list[int]:
+    """First global plane of each of `world` z-slabs, and nz (world + 1 ints)."""
+    out = (C.c_int * (world + 1))()
+    check(_lib_.lbm_slab_partition(int(nz), int(world), int(stencil), out))
+    return list(out)
+
+
+def lbm_slab_halo_mask(stencil: int, side: int, k: int) -> int:
+    """Bit mask of the populations ghost plane k (1..R+1) on side -1 / +1 must hold."""
+    m = C.c_uint()
+    check(_lib_.lbm_slab_halo_mask(int(stencil), int(side), int(k), C.byref(m)))
+    return m.value
+
+
+def lbm_set_populations_storage(ctx, host_f: np.ndarray, n0: float, scale: float):
+    f = np.ascontiguousarray(host_f, dtype=np.float64)
+    check(_lib_.lbm_set_populations_storage(ctx, _dptr(f), float(n0), float(scale)), ctx)
+
+
+def lbm_state_plane(ctx, i: int, z: int) -> tuple[int, int]:
+    """(device address, bytes) of population i's plane z of the current state."""
+    p = C.c_void_p()
+    nb = C.c_size_t()
+    check(_lib_.lbm_state_plane(ctx, int(i), int(z), C.byref(p), C.byref(nb)), ctx)
+    return p.value, nb.value
+
+
+def lbm_halo_copy(dst, dst_z: int, src, src_z: int, mask: int):
+    check(_lib_.lbm_halo_copy(dst, int(dst_z), src, int(src_z), int(mask)), dst)
+
+
 def lbm_tolman_fit(R_s, sigma_s, is_bubble, quadratic=True) -> tuple[float, float, float]:
     R = np.ascontiguousarray(R_s, dtype=np.float64)
     s = np.ascontiguousarray(sigma_s, dtype=np.float64)

@@ -48,3 +48,27 @@ def test_traffic_lookup_follows_the_source_hash(tmp_path, monkeypatch):
     assert b.measured_traffic("f16") is None                  # no summary for this storage
     (csrc / b.KERNEL_SOURCES[0]).write_text("// changed\n")
     assert b.measured_traffic("f32") is None                  # kernel changed since the capture
+
+
+def test_fp64_bound_is_measured_or_null(tmp_path, monkeypatch):
+    """The FP64 leg's bound comes from this run's DRAM fraction and, only when the
+    FP64 summary was captured on the current sources, its FP64-pipe figure."""
+    b = _bench_module()
+    csrc = tmp_path / "paper_2105_08772_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in b.KERNEL_SOURCES:
+        (csrc / f).write_text(f"// {f}\n")
+    import hashlib
+    h = hashlib.sha256(b"".join((csrc / f).read_bytes() for f in b.KERNEL_SOURCES)).hexdigest()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(b, "ROOT", tmp_path)
+    r = b.fp64_bound(500.0, 6800.0)
+    assert r["bound"] is None and "ncu" not in r["evidence"]          # no summary
+    assert abs(r["hbm_frac"] - 500.0 / 6800.0) < 1e-15
+    (prof / "lattice_moment_f64_128.md").write_text(
+        f"# summary\n\nfp64_pipe_pct: 81.1\nsource_sha256: {h}\n")
+    r = b.fp64_bound(500.0, 6800.0)
+    assert r["bound"] == "alu" and "81.1" in r["evidence"] and "lattice_moment_f64_128.md" in r["evidence"]
+    (csrc / b.KERNEL_SOURCES[1]).write_text("// changed\n")
+    assert b.fp64_bound(500.0, 6800.0)["bound"] is None                # stale summary
