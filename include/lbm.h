@@ -225,12 +225,14 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int reps, long long* choice);
 
 /* Select the step kernel's configuration by the code lbm_autotune reports:
  * kind * 10^8 + bx * 10^6 + by * 10^4 + (kind ? z chunk * 10 + prefetch depth : z chunk),
- * kind 0 the register-load kernel, 1 the cp.async-pipelined kernel, 2 the row-bulk
- * pipelined kernel, 4 the pipelined kernel with 16-byte row chunks, 5 the unit-tau
- * moment kernel (for tau != 1 the same code runs kind 4), 6 the unit-tau moment
- * kernel fed by element copies (any nx; two CTAs per SM; for tau != 1 the same
- * code runs kind 1).  Kinds 1-4 and 6: F32/F64 storage only, z chunk 0 = chosen
- * by the launcher; 2, 4 and 5 need nx % 4 == 0 and nx >= bx + 8; 6 is compiled
+ * kind 0 the register-load kernel, 1 the cp.async-pipelined kernel, 4 the
+ * pipelined kernel with 16-byte row chunks, 5 the unit-tau moment kernel (for
+ * tau != 1 the same code runs kind 4), 6 the unit-tau moment kernel fed by element
+ * copies (any nx; two CTAs per SM; for tau != 1 the same code runs kind 1), 7 the
+ * unit-tau kernel staged by TMA tensor-tile copies (F32, E4, tau = 1, 32 x 8
+ * tiles, nx % 4 == 0, nx >= 64, ny % 8 == 0, ny >= 16, nz >= 3; opt-in).  Kinds
+ * 1, 4, 6 and 7: F32/F64 storage only, z chunk 0 = chosen by the launcher; 4
+ * and 5 need nx % 4 == 0 and nx >= bx + 8; 6 is compiled
  * for 32 x 8 tiles with E4 (depth 1, and depth 2 in F32) and 32 x 4 with E6/E8
  * (depth 1).  Kind 5 also takes F16 storage (E4, 32 x 8 tiles, tau = 1,
  * nx % 8 == 0, nx >= 48).  The default (lbm_create) is kind 5 where it applies,
