@@ -325,8 +325,10 @@ lbm_status lbm_tolman_fit(const double* R_s, const double* sigma_s, const int* i
  * as one job: independent lattices of uneven boxes advance together, one launch of
  * the step kernel per time step for all of them (captured in a CUDA graph of
  * check_every launches), each until one of the two convergence tests of Sec. IV
- * holds.  Storage F64 or F32_SHIFTED; every lattice of a batch has the batch's
- * stencil and precision, and its own box, tau, G and psi.
+ * holds.  Every lattice of a batch has the batch's stencil and storage, and its
+ * own box, tau, G, psi and storage shift / scale.  F16_SHIFTED batches take E4
+ * and runs with tau = 1, nx % 8 == 0 and nx >= 48 (the FP16 moment kernel):
+ * lbm_batch_enqueue returns LBM_EINVAL for other runs.
  *
  * lbm_batch_workspace_bytes: device bytes for `slots` resident lattices whose
  * boxes fit max_box (0 for invalid arguments).  lbm_batch_create: the caller's
@@ -354,7 +356,8 @@ lbm_status lbm_batch_result(const lbm_batch* b, int id, lbm_obs* out);
 /* Batch autotuner: fills the slots from the queue, times `reps` (>= 2, rounded up
  * to even) launches of the batch step for every candidate -- kernel mode (the
  * row-chunk moment kernel, the element-copy moment kernel, the pipelined kernel,
- * where the queue allows each), z chunk (8, 16, 32 planes) and slot count (all
+ * where the queue allows each; F16: the moment kernel only), z chunk (8, 16, 32
+ * planes) and slot count (all
  * slots, or half of them when at least four lattices are resident) -- and keeps
  * the one with the most lattice updates per second for lbm_batch_run.  The
  * measured lattices are then started again from their initial drops (runs beyond

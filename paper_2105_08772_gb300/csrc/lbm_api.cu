@@ -1443,7 +1443,8 @@ BatchLayout batch_layout(int slots, lbm_box max_box, int stencil, int prec) {
 int natural_batch_mode(const lbm_batch* b);
 
 // the kernel modes that can run the whole queue, fastest first by construction
-std::vector<int> batch_modes_allowed(int natural) {
+std::vector<int> batch_modes_allowed(int natural, int prec) {
+  if (prec == kF16) return {kBatchMoment};   // the only FP16 batch kernel
   if (natural == kBatchMoment) return {kBatchMoment, kBatchMomentElem, kBatchUnitTau};
   if (natural == kBatchMomentElem) return {kBatchMomentElem, kBatchUnitTau};
   return {natural};
@@ -1452,7 +1453,7 @@ std::vector<int> batch_modes_allowed(int natural) {
 int batch_mode(const lbm_batch* b) {
   const int natural = natural_batch_mode(b);
   if (b->mode_override >= 0)
-    for (int m : batch_modes_allowed(natural))
+    for (int m : batch_modes_allowed(natural, b->prec))
       if (m == b->mode_override) return m;
   return natural;
 }
@@ -1581,7 +1582,7 @@ extern "C" {
 
 size_t lbm_batch_workspace_bytes(int slots, lbm_box max_box, int stencil, int prec) {
   if (slots < 1 || lbm_workspace_bytes(max_box, stencil, prec) == 0) return 0;
-  if (prec == kF16) return 0;   // batches run the pipelined kernel (FP32 / FP64 storage)
+  if (prec == kF16 && stencil != 4) return 0;   // FP16 batches: the E4 moment kernel only
   return batch_layout(slots, max_box, stencil, prec).total;
 }
 
@@ -1590,8 +1591,8 @@ lbm_status lbm_batch_create(int slots, lbm_box max_box, int stencil, int prec, v
   if (!out) return bfail(nullptr, LBM_EINVAL, "out is null");
   *out = nullptr;
   if (slots < 1) return bfail(nullptr, LBM_EINVAL, "slots must be >= 1");
-  if (!valid_stencil(stencil) || !valid_prec(prec) || prec == kF16)
-    return bfail(nullptr, LBM_EINVAL, "batches need stencil 4/6/8 and F64 or F32 storage");
+  if (!valid_stencil(stencil) || !valid_prec(prec) || (prec == kF16 && stencil != 4))
+    return bfail(nullptr, LBM_EINVAL, "batches need stencil 4/6/8 (4 for F16 storage)");
   if (!box_ok(max_box, stencil)) return bfail(nullptr, LBM_EINVAL, "max_box not allowed (sides >= 2R + 1, below 2^31 nodes)");
   const BatchLayout L = batch_layout(slots, max_box, stencil, prec);
   if (!dev_workspace) return bfail(nullptr, LBM_EINVAL, "workspace is null");
@@ -1635,6 +1636,8 @@ lbm_status lbm_batch_enqueue(lbm_batch* b, lbm_box box, double tau, double G, lb
   if (!center || !id) return bfail(b, LBM_EINVAL, "center and id must not be null");
   if (box.nx > b->max_box.nx || box.ny > b->max_box.ny || box.nz > b->max_box.nz || !box_ok(box, b->stencil))
     return bfail(b, LBM_EINVAL, "box %dx%dx%d does not fit the batch's slots", box.nx, box.ny, box.nz);
+  if (b->prec == kF16 && (tau != 1.0 || box.nx % 8 != 0 || box.nx < 48))
+    return bfail(b, LBM_EINVAL, "F16 batches take tau = 1 and nx %% 8 == 0, nx >= 48 (the FP16 moment kernel)");
   BatchRun r;
   r.box = box;
   r.tau = tau;
@@ -1723,7 +1726,7 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int reps, long long* choice) {
   int best_mode = natural, best_zc = 0, best_cap = b->slots;
   double best_rate = -1.0;
   const int save_cap = b->slot_cap;
-  for (int mode : batch_modes_allowed(natural)) {
+  for (int mode : batch_modes_allowed(natural, b->prec)) {
     for (int zc : {8, 16, 32}) {
       for (int cap : caps) {
         b->mode_override = mode;

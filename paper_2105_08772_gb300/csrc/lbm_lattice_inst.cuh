@@ -331,7 +331,9 @@ static cudaError_t launch_moment_batch_variant(const BatchEntry* table, const Ba
 template <int P, int ST>
 static cudaError_t dispatch_batch(int mode, const BatchEntry* table, const BatchHeader* hdr,
                                   int step, bool prepare, int* grid, cudaStream_t s) {
-  if constexpr (P == kF16) {
+  if constexpr (P == kF16) {   // FP16 storage: the moment kernel, E4, 32 x 8 tiles
+    if (ST == 4 && mode == kBatchMoment)
+      return launch_moment_batch_variant<P, 4, 32, 8, 1>(table, hdr, step, prepare, grid, s);
     return cudaErrorInvalidValue;
   } else if constexpr (P == kF32 && ST == 4) {
     if (mode == kBatchMoment) return launch_moment_batch_variant<P, ST, 32, 8, 1>(table, hdr, step, prepare, grid, s);

@@ -140,7 +140,7 @@ struct BatchHeader;
 // moment kernel with element copies)
 enum BatchMode : int { kBatchMixedTau = 0, kBatchUnitTau = 1, kBatchMoment = 2, kBatchMomentElem = 3 };
 inline TileCfg batch_tile(int prec, int stencil, int mode) {
-  TileCfg t{32, (stencil == 4 && (prec == kF32 || mode == kBatchMomentElem)) ? 8 : 4, 0};
+  TileCfg t{32, (stencil == 4 && (prec != kF64 || mode == kBatchMomentElem)) ? 8 : 4, 0};
   t.kind = mode == kBatchMoment ? 5 : (mode == kBatchMomentElem ? 6 : 1);
   return t;
 }
@@ -148,10 +148,13 @@ cudaError_t launch_batch_f64(int stencil, int mode, const BatchEntry* table, con
                              int step, bool prepare, int* grid, cudaStream_t s);
 cudaError_t launch_batch_f32(int stencil, int mode, const BatchEntry* table, const BatchHeader* hdr,
                              int step, bool prepare, int* grid, cudaStream_t s);
+cudaError_t launch_batch_f16(int stencil, int mode, const BatchEntry* table, const BatchHeader* hdr,
+                             int step, bool prepare, int* grid, cudaStream_t s);
 inline cudaError_t launch_batch(int prec, int stencil, int mode, const BatchEntry* table,
                                 const BatchHeader* hdr, int step, bool prepare, int* grid, cudaStream_t s) {
   if (prec == kF64) return launch_batch_f64(stencil, mode, table, hdr, step, prepare, grid, s);
   if (prec == kF32) return launch_batch_f32(stencil, mode, table, hdr, step, prepare, grid, s);
+  if (prec == kF16) return launch_batch_f16(stencil, mode, table, hdr, step, prepare, grid, s);
   return cudaErrorInvalidValue;
 }
 

@@ -96,8 +96,9 @@ def _rel(a, b):
 
 
 def configs(G: float = -5.0, rho_l: float = 2.0, rho_g: float = 0.15, max_steps: int = 50_000) -> dict:
-    """The 32^3 and 128^3 plain-method workloads (psi = 1 - exp(-n), E4, tau = 1, the literal
-    initial densities 2.0 / 0.15, unit interface width)."""
+    """The 32^3 and 128^3 plain-method workloads (psi = 1 - exp(-n), E4, tau = 1, unit
+    interface width): the literal initial densities 2.0 / 0.15, and at 128^3 also the
+    flat-interface coexistence densities of the same G."""
     keys = ("R_e", "dP", "R_s", "sigma_s", "n_in", "n_out", "mass", "max_u", "status_bits")
     out = {"G": G, "rho_l": rho_l, "rho_g": rho_g, "runs": []}
     lat = Lattice(32, 32, 32, G=G, prec="f64")
@@ -113,12 +114,18 @@ def configs(G: float = -5.0, rho_l: float = 2.0, rho_g: float = 0.15, max_steps:
                             "wall_s": wall, **{k: o[k] for k in keys}})
     finally:
         lat.close()
-    for prec in ("f64", "f32"):
-        for kind, (a, b) in (("droplet", (rho_l, rho_g)), ("bubble", (rho_g, rho_l))):
-            st, o, _, wall = _run_droplet(128, 32.0, a, b, prec, G, max_steps=max_steps)
-            out["runs"].append({"box": 128, "kind": kind, "R": 32.0, "prec": prec, "status": st,
-                                "steps": o["steps"], "criterion": o["criterion"], "wall_s": wall,
-                                "MLUPS": o["steps"] * 128 ** 3 / wall / 1e6, **{k: o[k] for k in keys}})
+    # the 128^3 runs from the literal densities and from the flat-interface ones
+    # (a bubble started in liquid at 2.0 > n_l takes up its gas and dissolves)
+    _, n_g, n_l, _, _ = flat_interface(G)
+    out["flat"] = {"n_g": n_g, "n_l": n_l}
+    for init, (hi, lo) in (("literal", (rho_l, rho_g)), ("flat", (n_l, n_g))):
+        for prec in ("f64", "f32"):
+            for kind, (a, b) in (("droplet", (hi, lo)), ("bubble", (lo, hi))):
+                st, o, _, wall = _run_droplet(128, 32.0, a, b, prec, G, max_steps=max_steps)
+                out["runs"].append({"box": 128, "kind": kind, "R": 32.0, "prec": prec, "init": init,
+                                    "status": st, "steps": o["steps"], "criterion": o["criterion"],
+                                    "wall_s": wall, "MLUPS": o["steps"] * 128 ** 3 / wall / 1e6,
+                                    **{k: o[k] for k in keys}})
     return out
 
 

@@ -188,3 +188,13 @@ def test_default_tile_rejects_what_create_rejects(args):
     with pytest.raises(_lib.LBMError) as e:
         P.lbm_default_tile(P.make_box(*box), stencil, prec, tau)
     assert e.value.status == _lib.LBM_EINVAL
+
+
+def test_batch_workspace_sizes_by_storage():
+    """FP16 batches exist for the E4 stencil only (the FP16 moment kernel)."""
+    box = P.make_box(64, 64, 64)
+    f16 = _lib.PRECS["f16"]
+    assert _lib.lib.lbm_batch_workspace_bytes(4, box, 4, f16) > 0
+    assert _lib.lib.lbm_batch_workspace_bytes(4, box, 6, f16) == 0
+    assert _lib.lib.lbm_batch_workspace_bytes(4, box, 4, _lib.PRECS["f32"]) > \
+        _lib.lib.lbm_batch_workspace_bytes(4, box, 4, f16)

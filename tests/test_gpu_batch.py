@@ -146,3 +146,36 @@ def test_autotuned_batch_equals_single_lattice_runs(prec):
             a, r = getattr(ob, k), getattr(ref, k)
             assert (a == r) or (np.isnan(a) and np.isnan(r)), (rid, k, a, r)
         lat.close()
+
+
+RUNS_F16 = [  # FP16 batches: tau = 1, nx % 8 == 0, nx >= 48
+    ((48, 40, 36), 1.0, -5.0, 9.0, 1.89, 0.12),
+    ((56, 24, 20), 1.0, -5.5, 5.0, 0.12, 1.89),     # bubble
+    ((64, 32, 16), 1.0, -4.6, 6.0, 1.70, 0.25),
+]
+
+
+def test_f16_batch_equals_single_lattice_runs():
+    """FP16-shifted batches run the FP16 moment kernel; each lattice keeps its own shift
+    and power-of-two scale and evolves bitwise as it does alone (kind 5, the batch's z
+    chunk)."""
+    steps, check = 384, 128
+    b = P.Batch(2, (64, 40, 36), prec="f16")
+    ids = [b.enqueue(box, tau=tau, G=G, R=R, rho_in=ri, rho_out=ro) for box, tau, G, R, ri, ro in RUNS_F16]
+    with pytest.raises(P.LBMError):
+        b.enqueue((40, 40, 40), tau=1.0, G=-5.0, R=8.0, rho_in=1.89, rho_out=0.12)   # nx < 48
+    with pytest.raises(P.LBMError):
+        b.enqueue((48, 40, 36), tau=0.8, G=-5.0, R=8.0, rho_in=1.89, rho_out=0.12)   # tau != 1
+    b.run(max_steps=steps, check_every=check, tol_dP_rel=-1.0, tol_du=-1.0)
+    for rid, (box, tau, G, R, ri, ro) in zip(ids, RUNS_F16):
+        st, ob = b.result(rid)
+        assert st == P._lib.LBM_ENOTCONV and ob.steps == steps, (rid, st, ob.steps)
+        lat = P.Lattice(*box, tau=tau, G=G, prec="f16")
+        lat.set_tile(532080001 + 10 * min(16, box[2]))
+        lat.init_drop((box[0] // 2, box[1] // 2, box[2] // 2), R, ri, ro)
+        lat.step(steps)
+        ref = lat.observables()
+        for k in STATE_KEYS:
+            a, r = getattr(ob, k), getattr(ref, k)
+            assert (a == r) or (np.isnan(a) and np.isnan(r)), (rid, k, a, r)
+        lat.close()

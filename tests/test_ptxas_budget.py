@@ -1,10 +1,11 @@
 """Register and spill budget of the default step kernels, from ptxas's own
-report (-Xptxas -v) of the FP32 translation unit compiled with the build's
-flags.  Occupancy is what the moment kernels are designed around:
+report (-Xptxas -v) of the FP32 and FP16 translation units compiled with the
+build's flags.  Occupancy is what the moment kernels are designed around:
   * kind 5, 32 x 8, depth 1: three 256-thread CTAs per SM need <= 85
     registers a thread (65536 / 768);
   * kind 5 depth 2 and kind 6 (element copies): two CTAs per SM, <= 128;
   * kind 7 (TMA tensor-tile copies), 32 x 8: three CTAs per SM, <= 85;
+  * FP16 kind 5, 32 x 8, depth 1: four CTAs per SM, <= 64;
 and none of them may spill or keep a local-memory stack frame (a run-time index
 into a constant table would put the table there).  A change that breaks a budget
 shows up here, on the CPU, before any GPU measurement.
@@ -43,13 +44,20 @@ def moment_kernels(tmp_path_factory):
         nvcc = b.nvcc()
     except RuntimeError:
         pytest.skip("nvcc not available")
-    obj = tmp_path_factory.mktemp("ptxas") / "lbm_lattice_f32.o"
-    cmd = [nvcc, *b.ARCH, *b.NVCC_FLAGS, "-Xptxas", "-v", "-c", str(PKG / "csrc" / "lbm_lattice_f32.cu"),
-           "-o", str(obj)]
-    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
-    assert r.returncode == 0, r.stderr[-2000:]
+    from concurrent.futures import ThreadPoolExecutor
+    tmp = tmp_path_factory.mktemp("ptxas")
+
+    def compile_tu(name):
+        cmd = [nvcc, *b.ARCH, *b.NVCC_FLAGS, "-Xptxas", "-v", "-c", str(PKG / "csrc" / f"{name}.cu"),
+               "-o", str(tmp / f"{name}.o")]
+        return subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+
+    with ThreadPoolExecutor(2) as ex:
+        rs = list(ex.map(compile_tu, ["lbm_lattice_f32", "lbm_lattice_f16"]))
+    for r in rs:
+        assert r.returncode == 0, r.stderr[-2000:]
     out, cur, spill = {}, None, (0, 0, 0)
-    for line in (r.stdout + r.stderr).splitlines():
+    for line in "\n".join(r.stdout + r.stderr for r in rs).splitlines():
         m = ENTRY.search(line)
         if m:
             cur, spill = m.group(1), (0, 0, 0)
@@ -80,6 +88,8 @@ def test_moment_kernels_do_not_spill(moment_kernels):
     (("lattice_moment_kernel", 1, 4, 32, 8, 1, 1), 128),       # kind 6, 2 CTAs/SM
     (("lattice_moment_batch_kernel", 1, 4, 32, 8, 1, 1), 128),
     (("lattice_tma_kernel", 4, 32, 8), 85),                    # kind 7, 3 CTAs/SM
+    (("lattice_moment_kernel", 2, 4, 32, 8, 1, 0), 64),        # FP16 kind 5, 4 CTAs/SM
+    (("lattice_moment_batch_kernel", 2, 4, 32, 8, 1, 0), 64),
 ])
 def test_register_budget_for_the_designed_occupancy(moment_kernels, key, limit):
     assert key in moment_kernels, sorted(moment_kernels)
