@@ -24,7 +24,9 @@ calls the library and collects the results.
 Command lines:  python -m paper_2105_08772_gb300.sweep --couplings -5.0 --radii 6:40:2
                 python -m paper_2105_08772_gb300.sweep --paper --max-L 157
 (--paper: the paper's own sweep, 12 reduced couplings x 2 pseudopotentials x odd
-boxes with R = L/4, and the power law delta = A eps^lambda of Sec. IV.)
+boxes with R = L/4, and the power law delta = A eps^lambda of Sec. IV.  Boxes
+above --big-L run only where the smaller ones cannot hold the wide interfaces,
+eps <= --big-eps, as a second batch whose slot count fits the device memory.)
 """
 from __future__ import annotations
 
@@ -168,9 +170,10 @@ def run_batched(runs, coex, slots: int = 64, prec: str = "f32", stencil: str = "
     """All runs through one lbm_batch (after lbm_batch_autotune if asked).  Returns
     (outcomes, wall seconds, lattice updates); the tuning time is in the wall time."""
     L = max(r.L for r in runs)
+    slots = min(slots, len(runs), slots_that_fit((L, L, L), stencil, prec))
     _sync()
     t0 = time.perf_counter()
-    b = Batch(min(slots, len(runs)), (L, L, L), stencil=stencil, prec=prec)
+    b = Batch(slots, (L, L, L), stencil=stencil, prec=prec)
     try:
         ids = []
         for r in runs:
@@ -188,6 +191,18 @@ def run_batched(runs, coex, slots: int = 64, prec: str = "f32", stencil: str = "
         b.close()
     _sync()
     return outs, time.perf_counter() - t0, lu
+
+
+def slots_that_fit(max_box, stencil: str = "E4", prec: str = "f32", share: float = 0.85) -> int:
+    """How many batch slots of max_box fit in `share` of the device's free memory."""
+    import torch
+    from ._lib import PRECS, STENCILS, lib
+    from .lbm import make_box
+    one = lib.lbm_batch_workspace_bytes(1, make_box(*max_box), STENCILS[stencil], PRECS[prec])
+    two = lib.lbm_batch_workspace_bytes(2, make_box(*max_box), STENCILS[stencil], PRECS[prec])
+    per_slot = max(two - one, 1)
+    free, _ = torch.cuda.mem_get_info()
+    return max(1, int((share * free - one) // per_slot) + 1)
 
 
 def run_plain(runs, coex, prec: str = "f64", stencil: str = "E4", max_steps: int = 50_000,
@@ -345,6 +360,10 @@ def main(argv=None) -> dict:
     ap.add_argument("--paper", action="store_true",
                     help="the paper's sweep: 12 reduced couplings x 2 psi x odd L (see --max-L)")
     ap.add_argument("--max-L", type=int, default=335, help="largest box side of --paper")
+    ap.add_argument("--big-L", type=int, default=213,
+                    help="--paper: boxes above this side run only at eps <= --big-eps, in a batch of their own")
+    ap.add_argument("--big-eps", type=float, default=0.038)
+    ap.add_argument("--big-max-steps", type=int, default=80_000)
     ap.add_argument("--distributed", action="store_true",
                     help="one process per GPU under torchrun: the runs are sharded over the ranks")
     a = ap.parse_args(argv)
@@ -360,6 +379,7 @@ def main(argv=None) -> dict:
     t0 = time.perf_counter()
     if a.paper:
         runs = plan_paper(sizes=tuple(L for L in PAPER_L if L <= a.max_L))
+        runs = [r for r in runs if r.L <= a.big_L or reduced_coupling(r) <= a.big_eps + 1e-9]
         coex = {}
         for p in PAPER_PSI:
             coex.update(coexistence(sorted({r.G for r in runs if r.psi == p}), psi=p))
@@ -370,8 +390,14 @@ def main(argv=None) -> dict:
         coex = coexistence(couplings, psi=a.psi)
     t_flat = time.perf_counter() - t0
     mine = shard(runs, rank, world)
-    outs, wall, lu = run_batched(mine, coex, slots=a.slots, prec=a.prec, max_steps=a.max_steps,
-                                 autotune=a.autotune)
+    # boxes above --big-L (paper sweep) take slots of their own size: a second batch
+    groups = [[r for r in mine if not a.paper or r.L <= a.big_L], [r for r in mine if a.paper and r.L > a.big_L]]
+    outs, wall, lu = [], 0.0, 0
+    for g, cap in zip(groups, (a.max_steps, max(a.max_steps, a.big_max_steps))):
+        if not g:
+            continue
+        o, w, n = run_batched(g, coex, slots=a.slots, prec=a.prec, max_steps=cap, autotune=a.autotune)
+        outs, wall, lu = outs + o, wall + w, lu + n
     if world > 1:
         outs = gather_outcomes(outs)
         wall = max_over_ranks(wall)
