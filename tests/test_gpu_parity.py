@@ -1,8 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Tolerances: density max-abs 1e-11 on the FP64 path and 1e-4 relative on the
-FP32-shifted path after 1000 steps.  FP16-shifted storage is checked against a
-bound derived from half precision (11-bit significand) and reported.
+FP32-shifted path after 1000 steps.  FP16-shifted storage is bounded by twice the
+error of the same storage in an FP64 model of the oracle (f16_storage_model).
 """
 import numpy as np
 import pytest
@@ -96,18 +96,45 @@ def test_parity_f32_shifted_1000_steps_random_state(random_state):
     assert rel < 1e-4, rel
 
 
-def test_parity_f16_shifted_1000_steps_droplet(droplet_state):
-    """Half storage rounds every shifted population to 2^-11 of its size each step; on the
-    droplet workload this accumulates to a few 1e-3 over 1000 steps (a plain numpy model of
-    the same storage gives 2.4e-3).  Bound: 1e-2."""
+def f16_storage_model(f0, steps, m):
+    """The oracle's step with FP16 storage emulated: after every step each population is
+    stored as (f_i - w_i n0) 2^k rounded to half precision (n0 the field's mean density,
+    2^k putting the largest deviation near 2^13, as the library chooses), in FP64
+    arithmetic otherwise.  The error of this model against the exact oracle is the
+    error FP16 storage itself makes."""
+    w = lbm3d.W[:, None, None, None]
+    n0 = float(lbm3d.density(f0).mean())
+    k = int(np.floor(np.log2(8192.0 / np.max(np.abs(f0 - w * n0)))))
+    q = lambda f: ((f - w * n0) * 2.0 ** k).astype(np.float16).astype(np.float64) / 2.0 ** k + w * n0  # noqa: E731
+    f = q(f0)
+    for _ in range(steps):
+        f = q(lbm3d.step(f, m))
+    return f
+
+
+@pytest.fixture(scope="module")
+def f16_model_error(droplet_state):
+    shape, c, f0, ref = droplet_state
+    rho_ref = lbm3d.density(ref)
+    emu = lbm3d.density(f16_storage_model(f0, 1000, oracle_model()))
+    return float(np.max(np.abs(emu - rho_ref) / rho_ref))
+
+
+def test_parity_f16_shifted_1000_steps_droplet(droplet_state, f16_model_error):
+    """FP16 storage against the FP64 oracle after 1000 steps, bounded by the error of the
+    same storage in an FP64 model (f16_storage_model): the kernels differ from that
+    model only by FP32 instead of FP64 arithmetic, 2^-24 against FP16's 2^-11 per
+    rounding, which can flip single roundings but not change the error's size.
+    Bound: twice the model's error."""
     shape, c, f0, ref = droplet_state
     lat = lattice(shape, prec="f16")
     lat.init_drop(c, 6.0, 1.8883, 0.1193, 1.0)
     lat.step(1000)
     rho_ref = lbm3d.density(ref)
     rel = np.max(np.abs(lat.rho() - rho_ref) / rho_ref)
-    print(f"f16 shifted droplet: max relative density error after 1000 steps {rel:.3e}")
-    assert np.isfinite(rel) and rel < 1e-2
+    print(f"f16 shifted droplet: max relative density error after 1000 steps {rel:.3e} "
+          f"(FP16 storage model {f16_model_error:.3e})")
+    assert np.isfinite(rel) and rel < 2.0 * f16_model_error
 
 
 def test_droplet_init_matches_oracle():
@@ -404,9 +431,13 @@ def droplet_state_48():
 
 def test_f16_moment_kernel_parity(droplet_state_48):
     """FP16 storage through the moment kernel (its default at tau = 1, nx % 8 == 0):
-    within the FP16 bound of the oracle (1e-2 after 1000 steps), and as close to the
-    register-load FP16 kernel."""
+    within twice the FP16 storage model's error of the oracle after 1000 steps (see
+    test_parity_f16_shifted_1000_steps_droplet), and as close to the register-load
+    FP16 kernel."""
     shape, c, f0, ref = droplet_state_48
+    rho_ref = lbm3d.density(ref)
+    bound = 2.0 * float(np.max(np.abs(lbm3d.density(f16_storage_model(f0, 1000, oracle_model())) - rho_ref)
+                               / rho_ref))
     a = lattice(shape, prec="f16")
     assert a.get_tile() // 100000000 == 5
     a.init_drop(c, 6.0, 1.8883, 0.1193, 1.0)
@@ -415,12 +446,12 @@ def test_f16_moment_kernel_parity(droplet_state_48):
     b.set_tile(32080016)                  # register-load kernel, 32 x 8, z chunk 16
     b.init_drop(c, 6.0, 1.8883, 0.1193, 1.0)
     b.step(1000)
-    rho_ref = lbm3d.density(ref)
     ra, rb = a.rho(), b.rho()
     rel = np.max(np.abs(ra - rho_ref) / rho_ref)
     ab = np.max(np.abs(ra - rb) / rho_ref)
-    print(f"f16 moment kernel: max relative density error {rel:.3e}; vs register-load kernel {ab:.3e}")
-    assert np.isfinite(rel) and rel < 1e-2 and ab < 1e-2
+    print(f"f16 moment kernel: max relative density error {rel:.3e}; vs register-load kernel {ab:.3e}; "
+          f"bound {bound:.3e}")
+    assert np.isfinite(rel) and rel < bound and ab < bound
 
 
 @pytest.mark.parametrize("prec,code,tau,shape", [(p, c, 1.0, sh) for p in ("f64", "f32")
