@@ -164,6 +164,7 @@ LatticeDesc desc_of(const lbm_ctx* c, int src_buf) {
   d.eos.T = c->eos.T;
   d.err = c->err_dev;
   d.tma = c->tma.ok ? &c->tma : nullptr;
+  set_float_params(d);
   return d;
 }
 

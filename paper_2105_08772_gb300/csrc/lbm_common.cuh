@@ -61,6 +61,9 @@ struct EosParams {
   int kind;
   double G;       // coupling (Eq. (8))
   double a, b, Rgas, T;  // Carnahan-Starling constants (kind == kPsiCS)
+  // the same constants rounded to float on the host (set_float_params), so that
+  // FP32 kernels take them straight from the parameter bank and convert nothing
+  float Gf, af, bf, RTf;
 };
 
 template <typename T>
@@ -81,11 +84,10 @@ template <>
 __device__ __forceinline__ float psi_of<float>(float n, const EosParams& e) {
   if (e.kind == kPsiOneMinusExp) return -expm1f(-n);
   if (e.kind == kPsiExpInv) return expf(-1.0f / n);
-  const float q = (float)e.b * n * 0.25f;
+  const float q = e.bf * n * 0.25f;
   const float om = 1.0f - q;
-  const float p = n * (float)(e.Rgas * e.T) * (1.0f + q + q * q - q * q * q) / (om * om * om) -
-                  (float)e.a * n * n;
-  return sqrtf(2.0f * (p - n * (1.0f / 3.0f)) / ((float)e.G * (1.0f / 3.0f)));
+  const float p = n * e.RTf * (1.0f + q + q * q - q * q * q) / (om * om * om) - e.af * n * n;
+  return sqrtf(2.0f * (p - n * (1.0f / 3.0f)) / (e.Gf * (1.0f / 3.0f)));
 }
 
 // ---------------------------------------------------------------- storage
@@ -127,9 +129,30 @@ struct LatticeDesc {
   double n0;            // storage shift (0 for F64)
   double scale;         // storage scale (1 for F64/F32)
   EosParams eos;
+  float n0f, omegaf, scalef, inv_scalef;   // n0, omega, scale, 1/scale rounded to float (host)
   int* err;             // device flag set by a kernel whose bounded wait ran out (may be null)
   const void* tma;      // host: the lattice's TMA tensor maps (TmaMaps) or null; kernels ignore it
 };
+
+// The float copies of a descriptor's double parameters; call after setting them.
+inline void set_float_params(LatticeDesc& d) {
+  d.n0f = (float)d.n0;
+  d.omegaf = (float)d.omega;
+  d.scalef = (float)d.scale;
+  d.inv_scalef = (float)(1.0 / d.scale);
+  d.eos.Gf = (float)d.eos.G;
+  d.eos.af = (float)d.eos.a;
+  d.eos.bf = (float)d.eos.b;
+  d.eos.RTf = (float)(d.eos.Rgas * d.eos.T);
+}
+
+// A descriptor parameter in the kernel's arithmetic type: the host-rounded float
+// copy for FP32 arithmetic, the double itself for FP64.
+template <typename T>
+__device__ __forceinline__ T dparam(double v, float f) {
+  if constexpr (sizeof(T) == 4) return f;
+  else return v;
+}
 
 constexpr int kMaxTmaMaps = 4;   // tensor maps per population buffer (TMA step kernel)
 

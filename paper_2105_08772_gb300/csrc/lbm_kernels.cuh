@@ -117,8 +117,8 @@ __device__ __forceinline__ void load_plane(const LatticeDesc& d, int x0, int y0,
   const S* __restrict__ src = static_cast<const S*>(d.src);
   const int nx = d.nx, ny = d.ny, nz = d.nz;
   const long long plane = d.plane;
-  const T inv_scale = (T)(1.0 / d.scale);
-  const T n0 = (T)d.n0;
+  const T inv_scale = dparam<T>(1.0 / d.scale, d.inv_scalef);
+  const T n0 = dparam<T>(d.n0, d.n0f);
   const int z = wrap(zg, nz);
   const int zm = wrap(z - 1, nz), zp = wrap(z + 1, nz);
   const int tid = threadIdx.x;
@@ -367,8 +367,8 @@ lattice_kernel(LatticeDesc d, int zchunk, ObsArgs oa) {
                               pops + ((kk + NP) % NP) * Q * NT, kk >= 0 && kk < zc);
   }
 
-  const T G = (T)d.eos.G, omega = (T)d.omega, n0 = (T)d.n0;
-  const T scale = (T)d.scale;
+  const T G = dparam<T>(d.eos.G, d.eos.Gf), omega = dparam<T>(d.omega, d.omegaf), n0 = dparam<T>(d.n0, d.n0f);
+  const T scale = dparam<T>(d.scale, d.scalef);
   const long long plane = d.plane;
   double acc_mass = 0, acc_w = 0, acc_wd0 = 0, acc_wd1 = 0, acc_wd2 = 0, acc_du = 0, acc_max = 0,
          acc_bad = 0;

@@ -62,7 +62,7 @@ __device__ __forceinline__ void chunk_process_item(const LatticeDesc& d, int zch
   const long long plane = d.plane;
   const S* __restrict__ src = static_cast<const S*>(d.src);
   S* __restrict__ dst = static_cast<S*>(d.dst);
-  const T n0 = (T)d.n0, G = (T)d.eos.G, omega = (T)d.omega;
+  const T n0 = dparam<T>(d.n0, d.n0f), G = dparam<T>(d.eos.G, d.eos.Gf), omega = dparam<T>(d.omega, d.omegaf);
   const int tiles_x = (nx + BX - 1) / BX;
   const int tid = threadIdx.x;
   const int tx = tid % BX, ty = tid / BX;

@@ -119,7 +119,7 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
   const long long plane = d.plane;
   const S* __restrict__ src = static_cast<const S*>(d.src);
   S* __restrict__ dst = static_cast<S*>(d.dst);
-  const T n0 = (T)d.n0, G = (T)d.eos.G;
+  const T n0 = dparam<T>(d.n0, d.n0f), G = dparam<T>(d.eos.G, d.eos.Gf);
   const int tiles_x = (nx + BX - 1) / BX;
   const int tid = threadIdx.x;
   const int tx = tid % BX, ty = tid / BX;
@@ -133,7 +133,7 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
   const bool active = tx < w && ty < h;
   const int rows = h + 2 * R;
   const int xa = x0 - APRON;
-  const T inv_scale = (T)(1.0 / d.scale), scale = (T)d.scale;
+  const T inv_scale = dparam<T>(1.0 / d.scale, d.inv_scalef), scale = dparam<T>(d.scale, d.scalef);
 
   // Copy positions are the chunked kernel's (one 16-byte chunk of a staged row).
   // Thread roles.  When the copy positions and the halo nodes fit in disjoint

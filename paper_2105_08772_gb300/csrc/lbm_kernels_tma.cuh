@@ -271,7 +271,7 @@ __device__ __forceinline__ bool tma_process_item(const LatticeDesc& d, const Tma
   const long long plane = d.plane;
   const float* __restrict__ src = static_cast<const float*>(d.src);
   float* __restrict__ dst = static_cast<float*>(d.dst);
-  const T n0 = (T)d.n0, G = (T)d.eos.G;
+  const T n0 = dparam<T>(d.n0, d.n0f), G = dparam<T>(d.eos.G, d.eos.Gf);
   const int tiles_x = (nx + BX - 1) / BX;
   const int tid = threadIdx.x;
   const int tx = tid % BX, ty = tid / BX;
