@@ -82,24 +82,23 @@ __device__ __forceinline__ int halo_node(int h) {
   return row * PX + (c < R ? c : PX - 2 * R + c);
 }
 
-// the same ring in warp-row order, for 32-wide tiles with R = 1: the first 32
-// nodes of the top halo row, the first 32 of the bottom row, the two remaining
-// nodes of each, then the side columns row by row -- each of the first two warps
-// reads one contiguous row (no bank conflicts there)
+// The same ring dealt to four halo warps, for 32-wide tiles with R = 1 and the
+// staged rows 44 floats apart: warp 0 reads the top halo row's first 32 nodes,
+// warp 1 the bottom row's, warp 2 the 16 side-column nodes (rows 1..8, x = 0 and
+// x = 33: 16 distinct banks), warp 3 the four remaining row-end nodes.  Each warp's
+// reads of one population hit distinct banks (a row 8 apart is 352 floats, a
+// multiple of 32, so the row-end nodes would share banks with the side columns
+// if one warp read both).  -1: lane without a node.
 template <int BX, int BY, int R>
-__device__ __forceinline__ int halo_node_rows(int h) {
-  static_assert(BX == 32 && R == 1, "warp-row order is defined for 32-wide tiles and R = 1");
+__device__ __forceinline__ int halo_node_warps(int h) {
+  static_assert(BX == 32 && BY == 8 && R == 1, "four-warp halo order is defined for 32 x 8 tiles and R = 1");
   constexpr int PX = BX + 2 * R, PY = BY + 2 * R;
+  if (h < 0) return -1;
   if (h < 32) return h;
-  h -= 32;
-  if (h < 32) return (PY - 1) * PX + h;
-  h -= 32;
-  if (h < PX - 32) return 32 + h;
-  h -= PX - 32;
-  if (h < PX - 32) return (PY - 1) * PX + 32 + h;
-  h -= PX - 32;
-  const int row = 1 + h / 2, c = h % 2;
-  return row * PX + (c == 0 ? 0 : PX - 1);
+  if (h < 64) return (PY - 1) * PX + (h - 32);
+  if (h < 80) return (1 + (h - 64) / 2) * PX + ((h & 1) ? PX - 1 : 0);
+  if (h >= 96 && h < 100) return ((h - 96) < 2 ? 0 : (PY - 1) * PX) + 32 + (h & 1);
+  return -1;
 }
 
 template <int P, int ST, int BX, int BY, int D, bool ELEM = false>
@@ -142,7 +141,9 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
   // loads to the barrier; otherwise two thread groups split the populations of
   // each position and the halo nodes go to the first threads.
   constexpr int POS = PY * NCH;
-  constexpr int POSW = (POS + 31) / 32 * 32, NHW = (NH + 31) / 32 * 32;
+  constexpr int POSW = (POS + 31) / 32 * 32;
+  constexpr bool HALO4 = !ELEM && BX == 32 && BY == 8 && R == 1 && POSW + 128 <= NT;   // halo_node_warps
+  constexpr int NHW = HALO4 ? 128 : (NH + 31) / 32 * 32;
   constexpr bool SPLIT = !ELEM && POSW + NHW <= NT;
   constexpr int NG = SPLIT ? 1 : ((2 * POS <= NT) ? 2 : 1);
   constexpr int NPP = NG == 2 ? 1 : (POS + NT - 1) / NT;
@@ -193,11 +194,15 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
 #pragma unroll
   for (int s = 0; s < NHPER; ++s) {
     const int hh = SPLIT ? (s == 0 ? tid - (NT - NHW) : -1) : tid + s * NT;
-    const bool mine = hh >= 0 && hh < NH;
-    if constexpr (SPLIT && BX == 32 && BY == 8 && R == 1)   // one contiguous row per halo warp
-      jh[s] = mine ? halo_node_rows<BX, BY, R>(hh) : 0;
-    else
+    bool mine;
+    if constexpr (HALO4) {   // bank-conflict-free halo warps
+      const int node = halo_node_warps<BX, BY, R>(hh);
+      mine = node >= 0;
+      jh[s] = mine ? node : 0;
+    } else {
+      mine = hh >= 0 && hh < NH;
       jh[s] = mine ? halo_node<R, PX, PY>(hh) : 0;
+    }
     validh[s] = mine && (jh[s] % PX) < w + 2 * R && (jh[s] / PX) < rows;
   }
   const int nplanes = zc + 2 * R;

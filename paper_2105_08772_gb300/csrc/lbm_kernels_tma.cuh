@@ -252,6 +252,26 @@ __device__ __forceinline__ bool tma_wait(unsigned long long* bar, unsigned par) 
 }
 
 // One work item (column, z chunk).  Returns false when a wait gave up.
+// The halo ring in warp-row order, for 32-wide tiles with R = 1: the first 32
+// nodes of the top halo row, the first 32 of the bottom row, the two remaining
+// nodes of each, then the side columns row by row (each of the first two warps
+// reads one contiguous row).
+template <int BX, int BY, int R>
+__device__ __forceinline__ int tma_halo_node_rows(int h) {
+  static_assert(BX == 32 && R == 1, "warp-row order is defined for 32-wide tiles and R = 1");
+  constexpr int PX = BX + 2 * R, PY = BY + 2 * R;
+  if (h < 32) return h;
+  h -= 32;
+  if (h < 32) return (PY - 1) * PX + h;
+  h -= 32;
+  if (h < PX - 32) return 32 + h;
+  h -= PX - 32;
+  if (h < PX - 32) return (PY - 1) * PX + 32 + h;
+  h -= PX - 32;
+  const int row = 1 + h / 2, c = h % 2;
+  return row * PX + (c == 0 ? 0 : PX - 1);
+}
+
 template <int ST, int BX, int BY>
 __device__ __forceinline__ bool tma_process_item(const LatticeDesc& d, const TmaMapSet& maps, int zchunk,
                                                  long long item, unsigned char* smem, unsigned& phase_bits) {
@@ -298,7 +318,7 @@ __device__ __forceinline__ bool tma_process_item(const LatticeDesc& d, const Tma
     const bool mine = hh >= 0 && hh < NH;
     int j = 0;
     if (mine) {
-      if constexpr (BX == 32 && BY == 8 && R == 1) j = halo_node_rows<BX, BY, R>(hh);
+      if constexpr (BX == 32 && BY == 8 && R == 1) j = tma_halo_node_rows<BX, BY, R>(hh);
       else j = halo_node<R, PX, PY>(hh);
     }
     jh[s] = j;

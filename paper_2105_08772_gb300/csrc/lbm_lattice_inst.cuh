@@ -43,13 +43,16 @@ inline int choose_zchunk(long long cols, int nz, int R, long long resident, int 
   return best_zc;
 }
 
-// Step kernels are launched with programmatic stream serialisation (each
-// begins with step_grid_enter): the next step's CTAs take the slots this
-// step's CTAs free and wait on the device for its completion, so consecutive
-// steps' launch latency and CTA ramp overlap the previous step's tail.
+// Step kernels whose CTAs take several work items in turn are launched with
+// programmatic stream serialisation (each kernel begins with step_grid_enter):
+// the next step's CTAs take the slots this step's CTAs free and wait on the
+// device for its completion, so consecutive steps' launch latency and CTA ramp
+// overlap the previous step's tail (256^3: 499 -> 488 us).  A grid of one item
+// per CTA has no such tail and measured 0.6 us slower with it (128^3), so it is
+// launched plainly.
 template <typename... KArgs, typename... Args>
 static cudaError_t launch_step_kernel(void (*kern)(KArgs...), long long grid, int threads, size_t smem,
-                                      cudaStream_t s, Args... args) {
+                                      cudaStream_t s, bool overlap, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3((unsigned)threads);
@@ -57,7 +60,7 @@ static cudaError_t launch_step_kernel(void (*kern)(KArgs...), long long grid, in
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[0].val.programmaticStreamSerializationAllowed = overlap ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, args...);
@@ -96,7 +99,7 @@ static cudaError_t launch_async_variant(const LatticeDesc& d, int zchunk, bool p
   const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
   const long long items = cols * ((d.nz + zc - 1) / zc);
   const long long grid = items < resident ? items : resident;
-  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, d, zc);
+  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, items > grid, d, zc);
 }
 
 template <int P, int ST, int BX, int BY, int D, bool UNIT_TAU>
@@ -116,7 +119,7 @@ static cudaError_t launch_chunk_variant(const LatticeDesc& d, int zchunk, bool p
   const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
   const long long items = cols * ((d.nz + zc - 1) / zc);
   const long long grid = items < resident ? items : resident;
-  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, d, zc);
+  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, items > grid, d, zc);
 }
 
 template <int P, int ST, int BX, int BY, int D>
@@ -154,7 +157,7 @@ static cudaError_t launch_moment(const LatticeDesc& d, int zchunk, bool prepare,
   const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
   const long long items = cols * ((d.nz + zc - 1) / zc);
   const long long grid = items < resident ? items : resident;
-  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, d, zc);
+  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, items > grid, d, zc);
 }
 
 template <int P, int ST>
@@ -243,7 +246,7 @@ static cudaError_t launch_moment_elem(const LatticeDesc& d, int zchunk, bool pre
   const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
   const long long items = cols * ((d.nz + zc - 1) / zc);
   const long long grid = items < resident ? items : resident;
-  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, d, zc);
+  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, items > grid, d, zc);
 }
 
 template <int P, int ST>
@@ -298,7 +301,7 @@ static cudaError_t launch_batch_variant(const BatchEntry* table, const BatchHead
   }
   if (grid) *grid = resident;
   if (prepare) return cudaSuccess;
-  return launch_step_kernel(kern, resident, Sh::NT, Sh::smem_bytes, s, table, hdr, step);
+  return launch_step_kernel(kern, resident, Sh::NT, Sh::smem_bytes, s, true, table, hdr, step);
 }
 
 template <int P, int ST, int BX, int BY, int D, bool ELEM = false>
@@ -323,7 +326,7 @@ static cudaError_t launch_moment_batch_variant(const BatchEntry* table, const Ba
   }
   if (grid) *grid = resident;
   if (prepare) return cudaSuccess;
-  return launch_step_kernel(kern, resident, Sh::NT, Sh::smem_bytes, s, table, hdr, step);
+  return launch_step_kernel(kern, resident, Sh::NT, Sh::smem_bytes, s, true, table, hdr, step);
 }
 
 // batches: the moment kernel when every lattice allows it, else the pipelined
@@ -386,7 +389,7 @@ static cudaError_t launch_tma(const LatticeDesc& d, int zchunk, bool prepare, cu
   const int zc = choose_zchunk(cols, d.nz, Sh::R, resident, zchunk);
   const long long items = cols * ((d.nz + zc - 1) / zc);
   const long long grid = items < resident ? items : resident;
-  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, d, maps, zc);
+  return launch_step_kernel(kern, grid, Sh::NT, Sh::smem_bytes, s, items > grid, d, maps, zc);
 }
 
 template <int P, int ST>

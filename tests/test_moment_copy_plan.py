@@ -46,10 +46,12 @@ def shape(BX, BY, R, S, ELEM):
     XWS = XW + 4 if (S == 4 and not ELEM and BX == 32 and BY == 8 and R == 1) else XW   # padded pitch
     NCH = XW // VE
     POS = PY * NCH
-    SPLIT = (not ELEM) and ceil32(POS) + ceil32(NH) <= NT
+    HALO4 = (not ELEM) and BX == 32 and BY == 8 and R == 1 and ceil32(POS) + 128 <= NT
+    NHW = 128 if HALO4 else ceil32(NH)
+    SPLIT = (not ELEM) and ceil32(POS) + NHW <= NT
     NG = 1 if SPLIT else (2 if 2 * POS <= NT else 1)
     return dict(NT=NT, PX=PX, PY=PY, NPAD=NPAD, NH=NH, NHPER=(NH + NT - 1) // NT, VE=VE, APRON=APRON,
-                XW=XW, XWS=XWS, NCH=NCH, POS=POS, POSW=ceil32(POS), NHW=ceil32(NH), SPLIT=SPLIT, NG=NG,
+                XW=XW, XWS=XWS, NCH=NCH, POS=POS, POSW=ceil32(POS), NHW=NHW, HALO4=HALO4, SPLIT=SPLIT, NG=NG,
                 NPP=1 if NG == 2 else (POS + NT - 1) // NT, ISPLIT=10 if NG == 2 else Q,
                 NPER=(NPAD + NT - 1) // NT,
                 stage_elems=Q * NPAD if ELEM else Q * PY * XWS)
@@ -66,23 +68,21 @@ def halo_node(h, R, PX, PY):
     return row * PX + (c if c < R else PX - 2 * R + c)
 
 
-def halo_node_rows(h, BX, BY, R):
-    """The warp-row order of the halo ring (32-wide tiles, R = 1)."""
+def halo_node_warps(h, BX, BY, R):
+    """The four-warp order of the halo ring (32 x 8 tiles, R = 1): top row, bottom
+    row, side columns, the four row ends; None for a lane without a node."""
     PX, PY = BX + 2 * R, BY + 2 * R
+    if h < 0:
+        return None
     if h < 32:
         return h
-    h -= 32
-    if h < 32:
-        return (PY - 1) * PX + h
-    h -= 32
-    if h < PX - 32:
-        return 32 + h
-    h -= PX - 32
-    if h < PX - 32:
-        return (PY - 1) * PX + 32 + h
-    h -= PX - 32
-    row, c = 1 + h // 2, h % 2
-    return row * PX + (0 if c == 0 else PX - 1)
+    if h < 64:
+        return (PY - 1) * PX + (h - 32)
+    if h < 80:
+        return (1 + (h - 64) // 2) * PX + (PX - 1 if h % 2 else 0)
+    if 96 <= h < 100:
+        return (0 if h - 96 < 2 else (PY - 1) * PX) + 32 + h % 2
+    return None
 
 
 def replay_plane(nx, ny, nz, BX, BY, R, S, ELEM, x0, y0, z):
@@ -140,11 +140,12 @@ def replay_plane(nx, ny, nz, BX, BY, R, S, ELEM, x0, y0, z):
             nodes.append((ty + R) * PX + (tx + R))
         for s in range(sh["NHPER"]):
             hh = (tid - (sh["NT"] - sh["NHW"]) if s == 0 else -1) if sh["SPLIT"] else tid + s * sh["NT"]
-            if 0 <= hh < sh["NH"]:
-                jh = (halo_node_rows(hh, BX, BY, R) if (sh["SPLIT"] and BX == 32 and BY == 8 and R == 1)
-                      else halo_node(hh, R, PX, PY))
-                if jh % PX < w + 2 * R and jh // PX < rows:
-                    nodes.append(jh)
+            if sh["HALO4"]:
+                jh = halo_node_warps(hh, BX, BY, R)
+            else:
+                jh = halo_node(hh, R, PX, PY) if 0 <= hh < sh["NH"] else None
+            if jh is not None and jh % PX < w + 2 * R and jh // PX < rows:
+                nodes.append(jh)
         for jn in nodes:
             assert jn not in formed, "a padded node is formed twice"
             hx, hy = jn % PX, jn // PX
@@ -204,7 +205,11 @@ def test_split_roles_are_disjoint_whole_warps(BX, BY, R, S, ELEM):
     if not sh["SPLIT"]:
         pytest.skip("this shape shares warps between copies and halo nodes")
     copy_threads = set(range(sh["POS"]))
-    halo_threads = {t for t in range(sh["NT"]) if 0 <= t - (sh["NT"] - sh["NHW"]) < sh["NH"]}
+    if sh["HALO4"]:
+        halo_threads = {t for t in range(sh["NT"])
+                        if halo_node_warps(t - (sh["NT"] - sh["NHW"]), BX, BY, R) is not None}
+    else:
+        halo_threads = {t for t in range(sh["NT"]) if 0 <= t - (sh["NT"] - sh["NHW"]) < sh["NH"]}
     assert not copy_threads & halo_threads
     assert max(copy_threads) // 32 < min(halo_threads) // 32      # different warps
     assert len(halo_threads) == sh["NH"]
@@ -261,3 +266,20 @@ def test_one_barrier_schedule(R, D, zc):
             m[0] = qd
             pz[2 * R] = qd
     assert collided == list(range(R, R + zc))                     # every output plane, in order
+
+
+def test_halo_warps_read_distinct_banks():
+    """FP32 32 x 8 stage (rows XWS = 44 floats apart): every halo warp's 19 population
+    reads hit 32 distinct banks (one wavefront each); the old three-warp order put the
+    row ends and the side columns in one warp, 4 two-way conflicts per read."""
+    sh = shape(32, 8, 1, 4, False)
+    assert sh["HALO4"] and sh["XWS"] == 44
+    PX, XWS, A = sh["PX"], sh["XWS"], sh["APRON"]
+    nodes = sorted({halo_node_warps(h, 32, 8, 1) for h in range(128)} - {None})
+    assert len(nodes) == sh["NH"]                        # the whole ring, once
+    for warp in range(4):
+        js = [halo_node_warps(h, 32, 8, 1) for h in range(32 * warp, 32 * warp + 32)]
+        js = [j for j in js if j is not None]
+        for i in range(Q):
+            banks = [((j // PX) * XWS + j % PX + A - 1 - XI[i, 0] + i * sh["PY"] * XWS) % 32 for j in js]
+            assert len(set(banks)) == len(banks), (warp, i)
