@@ -290,8 +290,12 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
       T g[Q];     // written, never read, by the unit-tau collision
       collide<T, true, true>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, (T)1);
       const long long node = ((long long)(z0 + k) * ny + (y0 + ty)) * nx + (x0 + tx);
+      S* q = dst + node;   // population i's plane is i * plane further on
 #pragma unroll
-      for (int i = 0; i < Q; ++i) Storage<P>::store(dst + i * plane + node, g[i], scale);
+      for (int i = 0; i < Q; ++i) {
+        Storage<P>::store(q, g[i], scale);
+        q += plane;
+      }
     }
 #pragma unroll
     for (int r = R; r > 0; --r) {
