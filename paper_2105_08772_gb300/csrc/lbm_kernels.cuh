@@ -249,9 +249,13 @@ __device__ __forceinline__ void sc_force(const typename Storage<P>::T* ring, con
 // exact arithmetic), so mass changes only by uncorrelated rounding.
 // UNIT_TAU: tau = 1 (the relaxation time the method uses); then 1 - omega = 0
 // and the post-collision populations depend on the old ones only through n, j.
-template <typename T, bool CLOSE_MASS, bool UNIT_TAU = false>
+// SCALED: the outputs come multiplied by wscale, a power of two (FP16 storage's
+// 2^k), folded into the weights and the mass closure; a power-of-two factor
+// commutes with every rounding, so the values are bitwise those of the
+// unscaled collision times wscale.
+template <typename T, bool CLOSE_MASS, bool UNIT_TAU = false, bool SCALED = false>
 __device__ __forceinline__ void collide(T* g, T dn, T n, T ux, T uy, T uz, T Fx, T Fy, T Fz,
-                                        T omega_in) {
+                                        T omega_in, T wscale = (T)1) {
   const T omega = UNIT_TAU ? (T)1 : omega_in;
   const T uu = ux * ux + uy * uy + uz * uz;
   const T uF = ux * Fx + uy * Fy + uz * Fz;
@@ -263,7 +267,7 @@ __device__ __forceinline__ void collide(T* g, T dn, T n, T ux, T uy, T uz, T Fx,
   for (int i = 1; i < Q; i += 2) {
     const T eu = (T)cx(i) * ux + (T)cy(i) * uy + (T)cz(i) * uz;
     const T eF = (T)cx(i) * Fx + (T)cy(i) * Fy + (T)cz(i) * Fz;
-    const T wi = (T)wq(i);
+    const T wi = SCALED ? (T)wq(i) * wscale : (T)wq(i);
     const T even = base + omega * (T)4.5 * n * eu * eu + (T)9 * cg * eu * eF;
     const T odd = (T)3 * (omega * n * eu + cg * eF);
     if (UNIT_TAU) {
@@ -276,8 +280,9 @@ __device__ __forceinline__ void collide(T* g, T dn, T n, T ux, T uy, T uz, T Fx,
   }
   if (CLOSE_MASS) {
     // pair sums first (their odd parts cancel), then the mirror-exact grouping
-    g[0] = dn - pair_sum9<T>(g[1] + g[2], g[3] + g[4], g[5] + g[6], g[7] + g[8], g[9] + g[10], g[11] + g[12],
-                             g[13] + g[14], g[15] + g[16], g[17] + g[18]);
+    g[0] = (SCALED ? dn * wscale : dn) -
+           pair_sum9<T>(g[1] + g[2], g[3] + g[4], g[5] + g[6], g[7] + g[8], g[9] + g[10], g[11] + g[12],
+                        g[13] + g[14], g[15] + g[16], g[17] + g[18]);
   }
 }
 

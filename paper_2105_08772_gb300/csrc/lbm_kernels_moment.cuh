@@ -62,11 +62,12 @@ struct MomentShape {
   static_assert((sizeof(S) * NS * stage_elems) % 16 == 0, "psi ring stays aligned");
 };
 
-// a staged (stored) value as an arithmetic value: FP16 storage is scaled by 2^k
+// a staged (stored) value as an arithmetic value, still scaled by FP16 storage's
+// 2^k: the density pass sums the scaled values and scales the sums once, which
+// gives bitwise the same sums (a power-of-two factor commutes with rounding)
 template <int P>
-__device__ __forceinline__ typename Storage<P>::T staged_value(typename Storage<P>::S x,
-                                                              typename Storage<P>::T inv_scale) {
-  if constexpr (P == kF16) return __half2float(x) * inv_scale;
+__device__ __forceinline__ typename Storage<P>::T staged_value(typename Storage<P>::S x) {
+  if constexpr (P == kF16) return __half2float(x);
   else return x;
 }
 
@@ -288,12 +289,14 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
       const T uy = (mjy[R] + (T)0.5 * Fy) * inv_n;
       const T uz = (mjz[R] + (T)0.5 * Fz) * inv_n;
       T g[Q];     // written, never read, by the unit-tau collision
-      collide<T, true, true>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, (T)1);
+      // FP16: the collision returns the populations times the storage scale
+      collide<T, true, true, P == kF16>(g, dn, n, ux, uy, uz, Fx, Fy, Fz, (T)1, scale);
       const long long node = ((long long)(z0 + k) * ny + (y0 + ty)) * nx + (x0 + tx);
       S* q = dst + node;   // population i's plane is i * plane further on
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
-        Storage<P>::store(q, g[i], scale);
+        if constexpr (P == kF16) *q = __float2half_rn(g[i]);   // already scaled
+        else Storage<P>::store(q, g[i], scale);
         q += plane;
       }
     }
@@ -313,14 +316,20 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
         T v[Q];
         if constexpr (ELEM) {
 #pragma unroll
-          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(st[i * NPAD + j0], inv_scale);
+          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(st[i * NPAD + j0]);
         } else {
           const S* row0 = st + (ty + R) * XWS + tx + APRON;
 #pragma unroll
-          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XWS - cx(i)], inv_scale);
+          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XWS - cx(i)]);
         }
         T dn, jx, jy, jz;
         moments(v, dn, jx, jy, jz);
+        if constexpr (P == kF16) {
+          dn *= inv_scale;
+          jx *= inv_scale;
+          jy *= inv_scale;
+          jz *= inv_scale;
+        }
         const T p = psi_of<T>(n0 + dn, d.eos);
         rs[j0] = p;
         pz[2 * R] = p;
@@ -335,14 +344,14 @@ __device__ __forceinline__ void moment_process_item(const LatticeDesc& d, int zc
         T v[Q];
         if constexpr (ELEM) {
 #pragma unroll
-          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(st[i * NPAD + jh[s]], inv_scale);
+          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(st[i * NPAD + jh[s]]);
         } else {
           const int hx = jh[s] % PX, hy = jh[s] / PX;
           const S* row0 = st + hy * XWS + hx + APRON - R;
 #pragma unroll
-          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XWS - cx(i)], inv_scale);
+          for (int i = 0; i < Q; ++i) v[i] = staged_value<P>(row0[i * PY * XWS - cx(i)]);
         }
-        rs[jh[s]] = psi_of<T>(n0 + sum19(v), d.eos);
+        rs[jh[s]] = psi_of<T>(n0 + (P == kF16 ? sum19(v) * inv_scale : sum19(v)), d.eos);
       }
     }
   }
