@@ -43,13 +43,14 @@ inline int choose_zchunk(long long cols, int nz, int R, long long resident, int 
   return best_zc;
 }
 
-// Step kernels whose CTAs take several work items in turn are launched with
-// programmatic stream serialisation (each kernel begins with step_grid_enter):
-// the next step's CTAs take the slots this step's CTAs free and wait on the
-// device for its completion, so consecutive steps' launch latency and CTA ramp
-// overlap the previous step's tail (256^3: 499 -> 488 us).  A grid of one item
-// per CTA has no such tail and measured 0.6 us slower with it (128^3), so it is
-// launched plainly.
+// Single-lattice step kernels whose CTAs take several work items in turn are
+// launched with programmatic stream serialisation (each kernel begins with
+// step_grid_enter): the next step's CTAs take the slots this step's CTAs free
+// and wait on the device for its completion, so consecutive steps' launch
+// latency and CTA ramp overlap the previous step's tail (256^3: 499 -> 488 us).
+// A grid of one item per CTA has no such tail and measured 0.6 us slower with it
+// (128^3), and the batch kernel measured 26% slower over a 144-lattice sweep, so
+// both are launched plainly.
 template <typename... KArgs, typename... Args>
 static cudaError_t launch_step_kernel(void (*kern)(KArgs...), long long grid, int threads, size_t smem,
                                       cudaStream_t s, bool overlap, Args... args) {
@@ -301,7 +302,7 @@ static cudaError_t launch_batch_variant(const BatchEntry* table, const BatchHead
   }
   if (grid) *grid = resident;
   if (prepare) return cudaSuccess;
-  return launch_step_kernel(kern, resident, Sh::NT, Sh::smem_bytes, s, true, table, hdr, step);
+  return launch_step_kernel(kern, resident, Sh::NT, Sh::smem_bytes, s, false, table, hdr, step);
 }
 
 template <int P, int ST, int BX, int BY, int D, bool ELEM = false>
@@ -326,7 +327,7 @@ static cudaError_t launch_moment_batch_variant(const BatchEntry* table, const Ba
   }
   if (grid) *grid = resident;
   if (prepare) return cudaSuccess;
-  return launch_step_kernel(kern, resident, Sh::NT, Sh::smem_bytes, s, true, table, hdr, step);
+  return launch_step_kernel(kern, resident, Sh::NT, Sh::smem_bytes, s, false, table, hdr, step);
 }
 
 // batches: the moment kernel when every lattice allows it, else the pipelined
