@@ -171,3 +171,21 @@ def test_single_slab_wraps_onto_itself():
         g = torch.from_numpy(storage_step(g.numpy(), _model("E4")))
         SL.exchange_tensors(p, 0, g)
         assert np.array_equal(g.numpy()[:, p.H:p.H + 9], ref[t])
+
+
+def test_slab_calls_reject_bad_arguments_on_the_host():
+    import ctypes as C
+    from paper_2105_08772_gb300 import _lib
+    L = _lib.lib
+    zb = (C.c_int * 4)()
+    m = C.c_uint()
+    assert L.lbm_slab_partition(12, 3, 4, None) == _lib.LBM_EINVAL
+    assert L.lbm_slab_partition(12, 0, 4, zb) == _lib.LBM_EINVAL
+    assert L.lbm_slab_partition(12, 3, 5, zb) == _lib.LBM_EINVAL          # no such stencil
+    assert L.lbm_slab_partition(12, 1, 4, zb) == _lib.LBM_OK and list(zb)[:2] == [0, 12]
+    assert L.lbm_slab_halo_mask(4, 0, 1, C.byref(m)) == _lib.LBM_EINVAL    # side must be +-1
+    assert L.lbm_slab_halo_mask(4, 1, 3, C.byref(m)) == _lib.LBM_EINVAL    # E4: k = 1, 2 only
+    assert L.lbm_slab_halo_mask(8, -1, 3, C.byref(m)) == _lib.LBM_OK and bin(m.value).count("1") == 5
+    assert L.lbm_slab_halo_mask(4, 1, 1, None) == _lib.LBM_EINVAL
+    assert L.lbm_halo_copy(None, 0, None, 0, 1) == _lib.LBM_EINVAL
+    assert L.lbm_state_plane(None, 0, 0, None, None) == _lib.LBM_EINVAL
